@@ -1,0 +1,381 @@
+"""Benchmark: zone-updates/s per SSP-RK3 step of the WENO5 MHD hot path.
+
+Workload (one GPU): 256^3 periodic decaying turbulence (seeded Gaussian
+velocity with per-mode variance |k|^-11/3 for 1<=|k|<=8 at rms Mach 0.5,
+log-normal density sigma 0.1, p = 1, B = (0.1,0,0) + solenoidal part at 10%
+of the kinetic energy), CFL 0.4.  One step = CFL reduction + dt + three
+stages of (x, y, z sweeps, update with constrained transport) + FP64
+conserved totals.  The headline value is the FP32-bulk path; the FP64 path,
+the FP32 L1 error against FP64 after 20 steps, the end-to-end number through
+host buffers, the ALU roofline of the dominant kernel and the CPU oracle are
+reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances an independent replica on its own
+GPU (weak scaling; the path needs no collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per RK step at 256^3 (FP32/learned vs FP64) at stated L1 error"
+UNIT = "zone-updates/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_PER_CLK = None   # measured (wb_alu_peak), see the design doc
+
+# Algorithmic FP operations of one interface of the sweep kernel (one
+# direction, one stage) and of one staged cell, counted from the kernel's
+# formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1); see the design doc.
+SWEEP_FLOPS_PER_INTERFACE = 1350
+SWEEP_FLOPS_PER_STAGED_CELL = 110
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path: str | None = None):
+        self.index = index
+        self.path = path
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        self.lines = [l.strip() for l in out.splitlines() if l.strip()]
+        if self.path:
+            with open(self.path, "w") as f:
+                f.write(self.Q + "\n" + "\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        busy = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sweep_units(n):
+    """(interfaces, staged cells) per launch of each sweep kernel at n^3."""
+    from paper_1808_10633_gb300 import wombat  # noqa: F401  (library must load)
+    iface = n ** 3
+    # x: tiles of 32 interfaces x 8 pencils stage 37 cells per pencil;
+    # y, z: tiles of 8 x 32 stage 13 cells per pencil.
+    staged = {"sweep_x": n ** 3 * 37 / 32, "sweep_y": n ** 3 * 13 / 8, "sweep_z": n ** 3 * 13 / 8}
+    return iface, staged
+
+
+def run_native(args, rank, world, local):
+    import torch
+
+    from paper_1808_10633_gb300 import inputs, wombat
+
+    n = args.size
+    st = inputs.turbulence(n, seed=1808)
+    zones = n ** 3
+    out = {}
+    clocks = Clocks(args.phys_gpu, os.path.join(args.out_dir, f"clocks_rank{rank}.csv") if args.out_dir else None)
+
+    peak32 = wombat.alu_peak_tflops("fp32")
+    peak64 = wombat.alu_peak_tflops("fp64")
+
+    # ---- FP32 bulk (headline) -------------------------------------------
+    g32 = wombat.Grid.from_state(st, precision="fp32")
+    for _ in range(args.warmup):
+        g32.step_cfl(args.cfl, 1)
+        g32.totals()
+    g32.sync()
+    with clocks:
+        barrier(world)
+        torch.cuda.synchronize()
+        tot_ms, kms, kcnt = g32.step_profiled(args.cfl, args.steps, with_totals=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        # FP64 path inside the same clock window
+        g64 = wombat.Grid.from_state(st, precision="fp64")
+        g64.step_cfl(args.cfl, 1)
+        g64.sync()
+        k64 = max(2, args.steps // 4)
+        tot64, kms64, kcnt64 = g64.step_profiled(args.cfl, k64, with_totals=True)
+    secs = max_over_ranks(tot_ms / 1e3, world)
+    value = world * zones * args.steps / secs
+    secs64 = max_over_ranks(tot64 / 1e3, world)
+    value64 = world * zones * k64 / secs64
+    clk = clocks.summary()
+
+    # graph-replay timing of the same step (no per-kernel events)
+    g32.sync()
+    t0 = time.perf_counter()
+    g32.step_cfl(args.cfl, args.steps)
+    g32.sync()
+    graph_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    def roofline(kms_, kcnt_, peak_tflops, label):
+        cls = max((k for k in ("sweep_x", "sweep_y", "sweep_z")), key=lambda k: kms_[k])
+        per_launch_ms = kms_[cls] / max(kcnt_[cls], 1)
+        iface, staged = sweep_units(n)
+        flops = iface * SWEEP_FLOPS_PER_INTERFACE + staged[cls] * SWEEP_FLOPS_PER_STAGED_CELL
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        return {"kernel": f"sweep_kernel<{label},{'xyz'[('sweep_x','sweep_y','sweep_z').index(cls)]}>",
+                "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                "flops_per_launch": flops, "ms_per_launch": round(per_launch_ms, 4),
+                "peak_source": "measured FMA throughput (wb_alu_peak) on this GPU"}
+
+    rf32 = roofline(kms, kcnt, peak32, "float")
+    rf64 = roofline(kms64, kcnt64, peak64, "double")
+    g64_state = None
+
+    # ---- FP32 vs FP64 L1 error after l1_steps fixed-dt steps (rank 0) ----
+    l1 = None
+    if rank == 0 and args.l1_steps > 0:
+        g64.set_state(st.U, np.stack([st.bx, st.by, st.bz]))
+        g32.set_state(st.U, np.stack([st.bx, st.by, st.bz]))
+        dt = g64.cfl_dt(args.cfl)
+        g64.step(dt, args.l1_steps)
+        g32.step(dt, args.l1_steps)
+        U64, _ = g64.get_state()
+        U32, _ = g32.get_state()
+        U64 = U64.reshape(8, -1)
+        U32 = U32.reshape(8, -1)
+        names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E"]
+        l1 = {}
+        for f, nm in enumerate(names):
+            d = np.abs(U32[f] - U64[f])
+            l1[nm] = {"l1_rel": float(d.mean() / max(np.abs(U64[f]).mean(), 1e-300)),
+                      "linf_rel": float(d.max() / max(np.abs(U64[f]).max(), 1e-300))}
+        g64_state = True
+    g64.close()
+
+    # ---- end to end through the ABI with pinned host buffers --------------
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.from_numpy(np.ascontiguousarray(st.U).ravel()).pin_memory()
+        bh = torch.from_numpy(np.stack([st.bx, st.by, st.bz]).ravel().copy()).pin_memory()
+        Uo = torch.empty(8 * zones, dtype=torch.float64).pin_memory()
+        bo = torch.empty(3 * zones, dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            g32.set_state(Uh, bh)
+            g32.step_cfl(args.cfl, 1)
+            g32.get_state(Uo, bo)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g32.set_state(Uh, bh)
+            g32.step_cfl(args.cfl, 1)
+            g32.get_state(Uo, bo)
+        el = time.perf_counter() - t0
+        barrier(world)
+        el = max_over_ranks(el, world)
+        e2e = {"value": world * zones * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(Uh.numel() * 8 + bh.numel() * 8),
+               "d2h_bytes_per_step": int(Uo.numel() * 8 + bo.numel() * 8),
+               "path": "wb_set_state(pinned FP64) + wb_step_cfl(1) + wb_get_state(pinned FP64)"}
+    g32.close()
+
+    launches_per_step = sum(kcnt.values()) / args.steps
+    out.update({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded turbulence generator, no dataset)",
+        "config": {"workload": f"decaying MHD turbulence {n}^3 periodic, SSP-RK3, CFL {args.cfl}, "
+                               "WENO5-JS characteristic sweeps + CT",
+                   "grid": [n, n, n], "precision": "fp32-bulk (fp64 islands)",
+                   "l2": "inputs larger than L2 (state 8 x 64 MiB fp32 + fluxes)",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(sum(kcnt.values())),
+        "launches_per_step": launches_per_step,
+        "graph_replay_ms_per_step": graph_ms,
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "roofline": rf32,
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": secs64 * 1e3 / k64, "steps": k64,
+                 "kernel_ms_per_step": {k: v / k64 for k, v in kms64.items()}, "roofline": rf64},
+        "fp32_vs_fp64_after_steps": args.l1_steps if l1 else 0,
+        "fp32_error_vs_fp64": l1,
+        "alu_peak_tflops": {"fp32": peak32, "fp64": peak64},
+        "clocks": clk,
+        "e2e": e2e,
+    })
+    return out
+
+
+def oracle_sample(seconds: float, n: int, cfl: float):
+    """Time the FP64 CPU oracle on an n^3 sample of the same workload until
+    `seconds` of wall time have elapsed (at least one step)."""
+    import oracle
+    from paper_1808_10633_gb300 import inputs
+
+    st = inputs.turbulence(n, seed=1808)
+    g = oracle.Grid(n, n, n, st.dx, st.dy, st.dz, st.gamma)
+    U, bx, by, bz = st.U, st.bx, st.by, st.bz
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        U, bx, by, bz, _ = oracle.step_cfl(g, U, bx, by, bz, cfl, nsteps=1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return n ** 3 * steps / el, steps, el, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the paper publishes no code, so the reference program is
+    the FP64 CPU oracle of the same scheme, timed on the host cores, each step
+    one SSP-RK3 step (with its CFL dt) of an n^3 sample of the workload."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1808_10633_gb300 import inputs
+
+    n = args.ref_size
+    st = inputs.turbulence(n, seed=1808)
+    g = oracle.Grid(n, n, n, st.dx, st.dy, st.dz, st.gamma)
+    U, bx, by, bz = st.U, st.bx, st.by, st.bz
+    for _ in range(args.warmup):
+        U, bx, by, bz, _ = oracle.step_cfl(g, U, bx, by, bz, args.cfl, nsteps=1)
+    t0 = time.perf_counter()
+    U, bx, by, bz, _ = oracle.step_cfl(g, U, bx, by, bz, args.cfl, nsteps=args.steps)
+    tot = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    value = n ** 3 * args.steps / tot
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded turbulence generator, no dataset)",
+            "config": {"workload": f"decaying MHD turbulence, FP64 CPU oracle on a {n}^3 sample of the "
+                                   f"{args.size}^3 workload, SSP-RK3, CFL {args.cfl}",
+                       "grid": [n, n, n]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} SSP-RK3 steps of a {n}^3 periodic turbulence sample"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--ref-size", type=int, default=64)
+    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--l1-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    # one GPU per rank: restrict this process to its GPU before CUDA starts,
+    # so that torch and the library see the same device 0
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    ids = vis.split(",") if vis else None
+    args.phys_gpu = int(ids[local]) if ids and local < len(ids) and ids[local].isdigit() else local
+    if args.impl == "native":
+        os.environ["CUDA_VISIBLE_DEVICES"] = str(args.phys_gpu)
+    if args.out_dir:
+        os.makedirs(args.out_dir, exist_ok=True)
+
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_1808_10633_gb300 import build
+    build.build()
+    res = run_native(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, s, el, cores = oracle_sample(args.cpu_seconds, args.ref_size, args.cfl)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{s} SSP-RK3 steps of a {args.ref_size}^3 periodic turbulence "
+                                         f"sample of the same generator, {el:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

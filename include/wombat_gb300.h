@@ -1,0 +1,176 @@
+/*
+ * wombat_gb300.h -- C ABI of the GB300 (sm_103a) WENO-Wombat MHD hot path.
+ *
+ * The library advances the ideal-MHD equations (Donnert et al. 2018,
+ * "Towards Exascale Simulations of the ICM Dynamo with WENO-Wombat",
+ * Sec. 2.1) on periodic Cartesian grids:
+ *   - fifth-order characteristic WENO flux sweeps along x, y, z (Sec. 2.1,
+ *     eq. FWENO with the interpolant phi_N and the Jiang-Shu weights; the
+ *     "rotated" sweeps of Sec. 2.2),
+ *   - local Lax-Friedrichs splitting per characteristic field (Sec. 2.1),
+ *   - constrained transport of the face-centred magnetic field on a
+ *     staggered mesh (Sec. 2.1),
+ *   - SSP-RK3 stages (or the classic four-stage RK4 of Sec. 2.1),
+ *   - a CFL time step and FP64 conserved totals.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns a wb_status; no exception or abort crosses the
+ *     ABI.  On failure wb_last_error() returns a message for the calling
+ *     thread.
+ *   - Host arrays belong to the caller and are copied; device memory is
+ *     allocated and owned by the library (released by wb_destroy).
+ *   - Work is ordered on the CUDA stream given at wb_init_grid.  Functions
+ *     marked "synchronises" wait for that stream before returning.
+ *   - Cell arrays use the layout [patch][8][nz][ny][nx] (x fastest), fields
+ *     (rho, mx, my, mz, Bx, By, Bz, E), E = p/(gamma-1) + rho|v|^2/2 +
+ *     |B|^2/2 (magnetic permeability absorbed).  Face arrays use
+ *     [patch][3][nz][ny][nx]: component 0 is b_x on the face (i-1/2, j, k),
+ *     1 is b_y on (i, j-1/2, k), 2 is b_z on (i, j, k-1/2).  Each patch is
+ *     periodic in every direction.  The cell-centred B is always the mean of
+ *     the two faces: the B entries of a cell array passed in are ignored and
+ *     those returned are recomputed from the faces.
+ *   - Values are FP64 at the ABI in every precision mode.
+ */
+#ifndef WOMBAT_GB300_H
+#define WOMBAT_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wb_grid wb_grid;   /* opaque, owned by the library */
+
+typedef enum {
+    WB_OK = 0,
+    WB_EINVAL = -1,       /* bad argument (null pointer, size, mode)          */
+    WB_ECUDA = -2,        /* a CUDA runtime call or kernel launch failed      */
+    WB_ENOMEM = -3,       /* device or pinned host allocation failed          */
+    WB_ENONFINITE = -4,   /* NaN/Inf or non-positive rho or p in the state    */
+    WB_ETIMEOUT = -5,     /* a bounded device wait gave up                    */
+    WB_EINTERNAL = -6     /* internal consistency check failed                */
+} wb_status;
+
+typedef enum {
+    WB_FP64 = 0,          /* whole path in FP64                               */
+    WB_FP32 = 1           /* state and sweeps in FP32; FP64 in the eigenvector
+                             normalisation near degenerate points, the CFL
+                             reduction and the conserved totals              */
+} wb_precision;
+
+typedef enum {
+    WB_SSPRK3 = 0,        /* three-stage SSP Runge-Kutta (Shu-Osher form)     */
+    WB_RK4 = 1            /* classic four-stage RK4 (Sec. 2.1)               */
+} wb_integrator;
+
+typedef struct {
+    int npatch;           /* number of independent periodic patches (>= 1)   */
+    const int *dims;      /* host, npatch*3 interior sizes (nx, ny, nz), each
+                             in [1, 4096]; copied                            */
+    double dx, dy, dz;    /* cell sizes (> 0), shared by all patches         */
+    double gamma;         /* ratio of specific heats (> 1), e.g. 5/3         */
+    int ghost;            /* stencil half-width + 1; must be 3 (WENO5)        */
+    int precision;        /* wb_precision                                    */
+    int integrator;       /* wb_integrator                                   */
+    int emf_mode;         /* 0: edge EMF = 1/2 sum of the 4 face EMFs - 1/4
+                             sum of the 4 cell values of -v x B (reduces to
+                             the 1-D upwind flux for grid-aligned flow);
+                             1: plain mean of the 4 face EMFs               */
+} wb_grid_desc;
+
+typedef struct {
+    int npatch;
+    long long ncells;     /* total cells over all patches                    */
+    int precision, integrator, emf_mode;
+    long long device_bytes; /* device memory held by the grid                */
+    double time;          /* simulated time advanced so far (device dt sum)  */
+    long long steps;      /* steps taken                                     */
+} wb_grid_info;
+
+/* Create a grid and upload the initial state.
+ * d: descriptor (Sec. 2.2 patches of a periodic world grid).  U0: host,
+ * cell array as above (B entries ignored).  b0: host, face array; its face
+ * divergence is preserved by the constrained transport.  cuda_stream: a
+ * cudaStream_t to order all work on, or NULL for a stream the library
+ * creates.  out: receives the grid.  Synchronises.
+ * Errors: WB_EINVAL for a null pointer, npatch < 1, a size out of range,
+ * ghost != 3, an unknown mode or non-positive dx/dy/dz or gamma <= 1;
+ * WB_ENOMEM; WB_ECUDA. */
+int wb_init_grid(const wb_grid_desc *d, const double *U0, const double *b0,
+                 void *cuda_stream, wb_grid **out);
+
+/* Replace the state with host arrays of the wb_init_grid layout.  Ordered on
+ * the grid's stream; pinned host arrays must stay valid until the next
+ * synchronising call, pageable ones are read before the call returns. */
+int wb_set_state(wb_grid *g, const double *U, const double *b);
+
+/* Advance nsteps steps of fixed size dt > 0 (Sec. 2.1 scheme; SSP-RK3 or
+ * RK4 per the descriptor).  Asynchronous on the grid's stream. */
+int wb_step(wb_grid *g, double dt, int nsteps);
+
+/* Advance nsteps steps, each with dt = cfl / max_cells sum_d (|v_d| +
+ * c_f,d) / dx_d taken on the device from the step's start state (no host
+ * round trip).  0 < cfl.  Asynchronous; a non-finite state is reported by
+ * the next synchronising call. */
+int wb_step_cfl(wb_grid *g, double cfl, int nsteps);
+
+/* dt = cfl / max_cells sum_d (|v_d| + c_f,d)/dx_d for the current state,
+ * FP64 max reduction.  Synchronises.  WB_ENONFINITE if any cell holds
+ * NaN/Inf or rho <= 0 or p <= 0. */
+int wb_cfl_dt(wb_grid *g, double cfl, double *dt_out);
+
+/* out[q] = sum over all cells of all patches of U_q * dx*dy*dz for the 8
+ * cell fields (B = face mean), deterministic FP64 reduction.  Synchronises.
+ * Also reports a non-finite state seen by an earlier asynchronous step. */
+int wb_conserved_totals(wb_grid *g, double out[8]);
+
+/* Copy the state to host arrays of the wb_init_grid layout (FP64).
+ * Either pointer may be NULL to skip it.  Synchronises. */
+int wb_get_state(wb_grid *g, double *U_out, double *b_out);
+
+/* Wait for the grid's stream; reports a non-finite state seen by an earlier
+ * asynchronous CFL step. */
+int wb_sync(wb_grid *g);
+
+/* Kernel classes timed by wb_step_profiled. */
+enum {
+    WB_K_SWEEP_X = 0,     /* x-sweep flux kernel (Sec. 2.1 eq. FWENO)         */
+    WB_K_SWEEP_Y = 1,
+    WB_K_SWEEP_Z = 2,
+    WB_K_UPDATE = 3,      /* flux difference + constrained transport + RK     */
+    WB_K_CFL = 4,         /* CFL max reduction                                */
+    WB_K_DT = 5,          /* dt from the reduced speed                        */
+    WB_K_TOTALS = 6,      /* conserved totals (two kernels)                   */
+    WB_NKERNEL = 7
+};
+
+/* Measurement helper: advance nsteps CFL steps exactly as wb_step_cfl does,
+ * but launch the kernels one by one (no graph) with a CUDA event pair
+ * recorded on the grid's stream around every launch; with_totals != 0 adds
+ * the conserved-totals reduction after every step.  kernel_ms[k] (host,
+ * WB_NKERNEL entries) receives the summed device time of class k,
+ * launches[k] its number of launches, *total_ms the device time from the
+ * first to the last event.  Synchronises. */
+int wb_step_profiled(wb_grid *g, double cfl, int nsteps, int with_totals,
+                     double *kernel_ms, int *launches, double *total_ms);
+
+/* Measurement helper, not part of the paper's method: FP32 (precision =
+ * WB_FP32) or FP64 (WB_FP64) fused multiply-add throughput of the current
+ * device in TFLOP/s, from a kernel of independent FMA chains timed with
+ * CUDA events (2 flops per FMA).  Synchronises the device. */
+int wb_alu_peak(int precision, double *tflops);
+
+int wb_get_info(wb_grid *g, wb_grid_info *info);
+
+/* Free all device memory of the grid (synchronises first).  NULL is a no-op. */
+int wb_destroy(wb_grid *g);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *wb_last_error(void);
+
+/* Library version string. */
+const char *wb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,558 @@
+// wb_abi.cu -- the C ABI (include/wombat_gb300.h): grid lifecycle and the
+// stream-ordered step sequence.
+//
+// Device state per grid (field-major over all patches, N cells in total):
+//   un   8 arrays  rho, mx, my, mz, E, bx, by, bz at t^n
+//   uk   8 arrays  Runge-Kutta stage state
+//   acc  8 arrays  RK4 accumulator (RK4 only)
+//   flux 21 arrays 7 face-flux components per axis
+//   er   3 arrays  cell -v x B for the edge EMFs (emf_mode 0 only)
+// One step = [CFL reduction + dt] + per stage: x, y, z sweeps and the
+// update kernel.  A step is captured once as a CUDA graph and replayed.
+#include "../../include/wombat_gb300.h"
+#include "wb_internal.h"
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define WB_CK(call)                                                                  \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? WB_ENOMEM : WB_ECUDA,      \
+                        "%s:%d: %s: %s", __FILE__, __LINE__, #call,                  \
+                        cudaGetErrorString(e_));                                     \
+    } while (0)
+
+constexpr int kPartials = 1024;
+
+// Optional per-launch CUDA-event timing (wb_step_profiled): an event pair is
+// recorded on the grid's stream around each kernel launch.
+struct Prof {
+    std::vector<cudaEvent_t> ev;   // 2 per launch
+    std::vector<int> cls;
+    size_t used = 0;
+};
+
+int prof_begin(Prof* pf, cudaStream_t s) {
+    if (!pf) return WB_OK;
+    if (pf->used + 2 > pf->ev.size()) return fail(WB_EINTERNAL, "profiler event pool exhausted");
+    WB_CK(cudaEventRecord(pf->ev[pf->used], s));
+    return WB_OK;
+}
+
+int prof_end(Prof* pf, cudaStream_t s, int cls) {
+    if (!pf) return WB_OK;
+    WB_CK(cudaEventRecord(pf->ev[pf->used + 1], s));
+    pf->cls.push_back(cls);
+    pf->used += 2;
+    return WB_OK;
+}
+
+}  // namespace
+
+struct wb_grid {
+    int npatch = 0;
+    long long N = 0;
+    double dx = 0, dy = 0, dz = 0, gamma = 0;
+    int precision = 0, integrator = 0, emf_mode = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t tsize = 8;
+    void* un = nullptr;
+    void* uk = nullptr;
+    void* acc = nullptr;
+    void* flux = nullptr;
+    void* er = nullptr;
+    wb::PatchDev* d_patches = nullptr;
+    std::vector<wb::PatchDev> h_patches;
+    wb::Tile* d_tiles[3] = {nullptr, nullptr, nullptr};
+    int ntiles[3] = {0, 0, 0};
+    wb::CellBlock* d_blocks = nullptr;
+    int nblocks = 0;
+    double* d_scalars = nullptr;          // dt, time
+    unsigned long long* d_smax = nullptr;
+    unsigned int* d_flag = nullptr;
+    double* d_partial = nullptr;          // kPartials*8 + 8 (totals)
+    double* d_io = nullptr;               // FP64 staging, 11 N
+    double* h_small = nullptr;            // pinned scratch for scalars
+    cudaGraphExec_t graph = nullptr;
+    int graph_mode = -1;                  // 0 fixed dt, 1 cfl
+    double graph_value = 0;
+    long long steps = 0;
+    long long bytes = 0;
+};
+
+namespace {
+
+template <class T>
+int enqueue_stages(wb_grid* g, Prof* pf) {
+    const long long N = g->N;
+    T* un = static_cast<T*>(g->un);
+    T* uk = static_cast<T*>(g->uk);
+    T* acc = static_cast<T*>(g->acc);
+    T* flux = static_cast<T*>(g->flux);
+    T* er = static_cast<T*>(g->er);
+    const int nstage = g->integrator == WB_RK4 ? 4 : 3;
+    for (int st = 0; st < nstage; st++) {
+        const T* src = st == 0 ? un : uk;
+        for (int axis = 0; axis < 3; axis++) {
+            wb::SweepArgs<T> a;
+            a.src = src;
+            a.flux = flux + (long long)axis * wb::kNFlux * N;
+            a.er = (axis == 0 && g->emf_mode == 0) ? er : nullptr;
+            a.tiles = g->d_tiles[axis];
+            a.patches = g->d_patches;
+            a.ncells = N;
+            a.gamma = g->gamma;
+            int rc = prof_begin(pf, g->stream);
+            if (rc != WB_OK) return rc;
+            WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+            if ((rc = prof_end(pf, g->stream, WB_K_SWEEP_X + axis)) != WB_OK) return rc;
+        }
+        wb::UpdateArgs<T> u;
+        u.un = un;
+        u.uk = src;
+        u.dst = (st == nstage - 1) ? un : uk;
+        u.acc = acc;
+        u.flux = flux;
+        u.er = g->emf_mode == 0 ? er : nullptr;
+        u.blocks = g->d_blocks;
+        u.patches = g->d_patches;
+        u.dt = g->d_scalars;
+        u.ncells = N;
+        u.idx = 1.0 / g->dx;
+        u.idy = 1.0 / g->dy;
+        u.idz = 1.0 / g->dz;
+        u.stage = st;
+        u.integrator = g->integrator;
+        u.emf_mode = g->emf_mode;
+        int rc = prof_begin(pf, g->stream);
+        if (rc != WB_OK) return rc;
+        WB_CK(wb::launch_update<T>(u, g->nblocks, g->stream));
+        if ((rc = prof_end(pf, g->stream, WB_K_UPDATE)) != WB_OK) return rc;
+    }
+    return WB_OK;
+}
+
+int enqueue_cfl(wb_grid* g, Prof* pf = nullptr) {
+    int rc = prof_begin(pf, g->stream);
+    if (rc != WB_OK) return rc;
+    WB_CK(cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->stream));
+    if (g->precision == WB_FP64)
+        WB_CK(wb::launch_cfl<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches,
+                                     g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
+                                     g->gamma, g->d_smax, g->d_flag, g->stream));
+    else
+        WB_CK(wb::launch_cfl<float>(static_cast<const float*>(g->un), g->d_blocks, g->d_patches,
+                                    g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
+                                    g->gamma, g->d_smax, g->d_flag, g->stream));
+    return prof_end(pf, g->stream, WB_K_CFL);
+}
+
+int enqueue_totals(wb_grid* g, Prof* pf = nullptr) {
+    double* res = g->d_partial + kPartials * 8;
+    const double dV = g->dx * g->dy * g->dz;
+    int rc = prof_begin(pf, g->stream);
+    if (rc != WB_OK) return rc;
+    if (g->precision == WB_FP64)
+        WB_CK(wb::launch_totals<double>(static_cast<const double*>(g->un), g->d_patches, g->npatch,
+                                        g->N, g->d_partial, kPartials, dV, res, g->stream));
+    else
+        WB_CK(wb::launch_totals<float>(static_cast<const float*>(g->un), g->d_patches, g->npatch,
+                                       g->N, g->d_partial, kPartials, dV, res, g->stream));
+    return prof_end(pf, g->stream, WB_K_TOTALS);
+}
+
+// One step: mode 0 fixed dt = value, mode 1 dt = value / smax.
+int enqueue_step(wb_grid* g, int mode, double value, Prof* pf = nullptr) {
+    int rc;
+    if (mode == 1) {
+        if ((rc = enqueue_cfl(g, pf)) != WB_OK) return rc;
+        if ((rc = prof_begin(pf, g->stream)) != WB_OK) return rc;
+        WB_CK(wb::launch_set_dt(g->d_smax, value, 0.0, g->d_scalars, g->d_scalars + 1, g->stream));
+    } else {
+        if ((rc = prof_begin(pf, g->stream)) != WB_OK) return rc;
+        WB_CK(wb::launch_set_dt(g->d_smax, 0.0, value, g->d_scalars, g->d_scalars + 1, g->stream));
+    }
+    if ((rc = prof_end(pf, g->stream, WB_K_DT)) != WB_OK) return rc;
+    return g->precision == WB_FP64 ? enqueue_stages<double>(g, pf) : enqueue_stages<float>(g, pf);
+}
+
+int capture_step(wb_grid* g, int mode, double value) {
+    if (g->graph && g->graph_mode == mode && g->graph_value == value) return WB_OK;
+    if (g->graph) {
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    WB_CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(g, mode, value);
+    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (rc != WB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    WB_CK(ce);
+    cudaError_t ie = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    WB_CK(ie);
+    g->graph_mode = mode;
+    g->graph_value = value;
+    return WB_OK;
+}
+
+int run_steps(wb_grid* g, int mode, double value, int nsteps) {
+    WB_CK(cudaSetDevice(g->device));
+    int rc = capture_step(g, mode, value);
+    if (rc != WB_OK) return rc;
+    for (int s = 0; s < nsteps; s++) WB_CK(cudaGraphLaunch(g->graph, g->stream));
+    g->steps += nsteps;
+    return WB_OK;
+}
+
+int check_flag(wb_grid* g) {
+    WB_CK(cudaMemcpyAsync(g->h_small, g->d_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                          g->stream));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    unsigned int f = *reinterpret_cast<unsigned int*>(g->h_small);
+    if (f) {
+        WB_CK(cudaMemsetAsync(g->d_flag, 0, sizeof(unsigned int), g->stream));
+        WB_CK(cudaStreamSynchronize(g->stream));
+        return fail(WB_ENONFINITE, "state holds %s",
+                    (f & 1u) ? "NaN/Inf values" : "non-positive density or pressure");
+    }
+    return WB_OK;
+}
+
+int upload(wb_grid* g, const double* U, const double* b) {
+    const long long N = g->N;
+    WB_CK(cudaMemcpyAsync(g->d_io, U, sizeof(double) * 8 * N, cudaMemcpyHostToDevice, g->stream));
+    WB_CK(cudaMemcpyAsync(g->d_io + 8 * N, b, sizeof(double) * 3 * N, cudaMemcpyHostToDevice,
+                          g->stream));
+    if (g->precision == WB_FP64)
+        WB_CK(wb::launch_import<double>(g->d_io, g->d_io + 8 * N, static_cast<double*>(g->un),
+                                        g->d_blocks, g->d_patches, N, g->nblocks, g->stream));
+    else
+        WB_CK(wb::launch_import<float>(g->d_io, g->d_io + 8 * N, static_cast<float*>(g->un),
+                                       g->d_blocks, g->d_patches, N, g->nblocks, g->stream));
+    return WB_OK;
+}
+
+void release(wb_grid* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->d_patches, g->d_tiles[0],
+                    g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_scalars, g->d_smax,
+                    g->d_flag, g->d_partial, g->d_io};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->h_small) cudaFreeHost(g->h_small);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+template <class P>
+int dmalloc(wb_grid* g, P** p, size_t bytes) {
+    WB_CK(cudaMalloc(reinterpret_cast<void**>(p), bytes));
+    g->bytes += (long long)bytes;
+    return WB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wb_last_error(void) { return g_err.c_str(); }
+
+const char* wb_version(void) { return "wombat-gb300 0.1 (sm_103a)"; }
+
+int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void* cuda_stream,
+                 wb_grid** out) {
+    g_err.clear();
+    if (!d || !U0 || !b0 || !out) return fail(WB_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->npatch < 1 || !d->dims) return fail(WB_EINVAL, "npatch must be >= 1 with dims");
+    if (d->ghost != 3) return fail(WB_EINVAL, "ghost must be 3 (WENO5 stencil), got %d", d->ghost);
+    if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return fail(WB_EINVAL, "dx, dy, dz must be > 0");
+    if (!(d->gamma > 1.0)) return fail(WB_EINVAL, "gamma must be > 1");
+    if (d->precision != WB_FP64 && d->precision != WB_FP32)
+        return fail(WB_EINVAL, "unknown precision %d", d->precision);
+    if (d->integrator != WB_SSPRK3 && d->integrator != WB_RK4)
+        return fail(WB_EINVAL, "unknown integrator %d", d->integrator);
+    if (d->emf_mode != 0 && d->emf_mode != 1) return fail(WB_EINVAL, "unknown emf_mode %d", d->emf_mode);
+
+    wb_grid* g = new (std::nothrow) wb_grid();
+    if (!g) return fail(WB_ENOMEM, "host allocation failed");
+    g->npatch = d->npatch;
+    g->dx = d->dx; g->dy = d->dy; g->dz = d->dz; g->gamma = d->gamma;
+    g->precision = d->precision; g->integrator = d->integrator; g->emf_mode = d->emf_mode;
+    g->tsize = d->precision == WB_FP64 ? 8 : 4;
+    long long off = 0;
+    for (int p = 0; p < d->npatch; p++) {
+        const int nx = d->dims[3 * p], ny = d->dims[3 * p + 1], nz = d->dims[3 * p + 2];
+        if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) {
+            delete g;
+            return fail(WB_EINVAL, "patch %d: sizes (%d,%d,%d) outside [1,4096]", p, nx, ny, nz);
+        }
+        const long long np = (long long)nx * ny * nz;
+        if (np >= (1LL << 31)) {
+            delete g;
+            return fail(WB_EINVAL, "patch %d: more than 2^31-1 cells", p);
+        }
+        g->h_patches.push_back(wb::PatchDev{nx, ny, nz, 0, off});
+        off += np;
+    }
+    g->N = off;
+
+    int rc;
+    auto bail = [&](int code) { release(g); return code; };
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return fail(WB_ECUDA, "no CUDA device available");
+    }
+    if (cuda_stream) {
+        g->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete g;
+            return fail(WB_ECUDA, "stream creation failed");
+        }
+        g->own_stream = true;
+    }
+    // tiles and cell blocks
+    std::vector<wb::Tile> tiles[3];
+    std::vector<wb::CellBlock> blocks;
+    for (int p = 0; p < g->npatch; p++) {
+        const wb::PatchDev& P = g->h_patches[p];
+        int ta, tp;
+        wb::sweep_tile_shape(0, &ta, &tp);
+        for (int z = 0; z < P.nz; z++)
+            for (int y0 = 0; y0 < P.ny; y0 += tp)
+                for (int x0 = 0; x0 < P.nx; x0 += ta) tiles[0].push_back(wb::Tile{p, x0, y0, z});
+        wb::sweep_tile_shape(1, &ta, &tp);
+        for (int z = 0; z < P.nz; z++)
+            for (int y0 = 0; y0 < P.ny; y0 += ta)
+                for (int x0 = 0; x0 < P.nx; x0 += tp) tiles[1].push_back(wb::Tile{p, y0, x0, z});
+        wb::sweep_tile_shape(2, &ta, &tp);
+        for (int y = 0; y < P.ny; y++)
+            for (int z0 = 0; z0 < P.nz; z0 += ta)
+                for (int x0 = 0; x0 < P.nx; x0 += tp) tiles[2].push_back(wb::Tile{p, z0, x0, y});
+        const long long np = (long long)P.nx * P.ny * P.nz;
+        for (long long c = 0; c < np; c += wb::kCellBlock) blocks.push_back(wb::CellBlock{p, (int)c});
+    }
+    for (int a = 0; a < 3; a++) {
+        if (tiles[a].size() > 0x7fffffffULL) return bail(fail(WB_EINVAL, "grid too large"));
+        g->ntiles[a] = (int)tiles[a].size();
+    }
+    g->nblocks = (int)blocks.size();
+
+    const size_t T = g->tsize;
+    const long long N = g->N;
+    if ((rc = dmalloc(g, &g->un, T * 8 * N))) return bail(rc);
+    if ((rc = dmalloc(g, &g->uk, T * 8 * N))) return bail(rc);
+    if (g->integrator == WB_RK4 && (rc = dmalloc(g, &g->acc, T * 8 * N))) return bail(rc);
+    if ((rc = dmalloc(g, &g->flux, T * 3 * wb::kNFlux * N))) return bail(rc);
+    if (g->emf_mode == 0 && (rc = dmalloc(g, &g->er, T * 3 * N))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_patches, sizeof(wb::PatchDev) * g->npatch))) return bail(rc);
+    for (int a = 0; a < 3; a++)
+        if ((rc = dmalloc(g, &g->d_tiles[a], sizeof(wb::Tile) * tiles[a].size()))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_blocks, sizeof(wb::CellBlock) * blocks.size()))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_scalars, sizeof(double) * 2))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_smax, sizeof(unsigned long long)))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_flag, sizeof(unsigned int)))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_partial, sizeof(double) * (kPartials * 8 + 8)))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_io, sizeof(double) * 11 * N))) return bail(rc);
+    if (cudaMallocHost(reinterpret_cast<void**>(&g->h_small), 256) != cudaSuccess)
+        return bail(fail(WB_ENOMEM, "pinned host allocation failed"));
+
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream);
+    };
+    if (cp(g->d_patches, g->h_patches.data(), sizeof(wb::PatchDev) * g->npatch) != cudaSuccess ||
+        cp(g->d_blocks, blocks.data(), sizeof(wb::CellBlock) * blocks.size()) != cudaSuccess)
+        return bail(fail(WB_ECUDA, "table upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+    for (int a = 0; a < 3; a++)
+        if (cp(g->d_tiles[a], tiles[a].data(), sizeof(wb::Tile) * tiles[a].size()) != cudaSuccess)
+            return bail(fail(WB_ECUDA, "tile upload failed"));
+    if (cudaMemsetAsync(g->d_scalars, 0, sizeof(double) * 2, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_flag, 0, sizeof(unsigned int), g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->flux, 0, T * 3 * wb::kNFlux * N, g->stream) != cudaSuccess)
+        return bail(fail(WB_ECUDA, "memset failed"));
+    cudaError_t pe = g->precision == WB_FP64 ? wb::prepare_sweep_kernels<double>()
+                                             : wb::prepare_sweep_kernels<float>();
+    if (pe != cudaSuccess) return bail(fail(WB_ECUDA, "kernel attributes: %s", cudaGetErrorString(pe)));
+    if ((rc = upload(g, U0, b0)) != WB_OK) return bail(rc);
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess)
+        return bail(fail(WB_ECUDA, "init: %s", cudaGetErrorString(cudaGetLastError())));
+    *out = g;
+    return WB_OK;
+}
+
+int wb_set_state(wb_grid* g, const double* U, const double* b) {
+    g_err.clear();
+    if (!g || !U || !b) return fail(WB_EINVAL, "null argument");
+    WB_CK(cudaSetDevice(g->device));
+    return upload(g, U, b);
+}
+
+int wb_step(wb_grid* g, double dt, int nsteps) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (!(dt > 0) || nsteps < 0) return fail(WB_EINVAL, "need dt > 0 and nsteps >= 0");
+    return run_steps(g, 0, dt, nsteps);
+}
+
+int wb_step_cfl(wb_grid* g, double cfl, int nsteps) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (!(cfl > 0) || nsteps < 0) return fail(WB_EINVAL, "need cfl > 0 and nsteps >= 0");
+    return run_steps(g, 1, cfl, nsteps);
+}
+
+int wb_step_profiled(wb_grid* g, double cfl, int nsteps, int with_totals, double* kernel_ms,
+                     int* launches, double* total_ms) {
+    g_err.clear();
+    if (!g || !kernel_ms || !launches || !total_ms) return fail(WB_EINVAL, "null argument");
+    if (!(cfl > 0) || nsteps < 1) return fail(WB_EINVAL, "need cfl > 0 and nsteps >= 1");
+    WB_CK(cudaSetDevice(g->device));
+    const int per_step = 2 + (g->integrator == WB_RK4 ? 4 : 3) * 4 + (with_totals ? 1 : 0);
+    Prof pf;
+    pf.ev.resize((size_t)2 * per_step * nsteps, nullptr);
+    int rc = WB_OK;
+    for (auto& e : pf.ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            rc = fail(WB_ECUDA, "event creation failed");
+            break;
+        }
+    }
+    for (int s = 0; s < nsteps && rc == WB_OK; s++) {
+        rc = enqueue_step(g, 1, cfl, &pf);
+        if (rc == WB_OK && with_totals) rc = enqueue_totals(g, &pf);
+    }
+    if (rc == WB_OK && cudaStreamSynchronize(g->stream) != cudaSuccess)
+        rc = fail(WB_ECUDA, "profiled step: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == WB_OK) {
+        for (int k = 0; k < WB_NKERNEL; k++) { kernel_ms[k] = 0.0; launches[k] = 0; }
+        for (size_t l = 0; l < pf.cls.size(); l++) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, pf.ev[2 * l], pf.ev[2 * l + 1]);
+            kernel_ms[pf.cls[l]] += ms;
+            launches[pf.cls[l]] += 1;
+        }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, pf.ev[0], pf.ev[pf.used - 1]);
+        *total_ms = tot;
+        g->steps += nsteps;
+    }
+    for (auto& e : pf.ev)
+        if (e) cudaEventDestroy(e);
+    if (rc != WB_OK) return rc;
+    return check_flag(g);
+}
+
+int wb_cfl_dt(wb_grid* g, double cfl, double* dt_out) {
+    g_err.clear();
+    if (!g || !dt_out) return fail(WB_EINVAL, "null argument");
+    if (!(cfl > 0)) return fail(WB_EINVAL, "need cfl > 0");
+    WB_CK(cudaSetDevice(g->device));
+    int rc = enqueue_cfl(g);
+    if (rc != WB_OK) return rc;
+    WB_CK(cudaMemcpyAsync(g->h_small + 1, g->d_smax, sizeof(double), cudaMemcpyDeviceToHost,
+                          g->stream));
+    if ((rc = check_flag(g)) != WB_OK) return rc;
+    double smax;
+    std::memcpy(&smax, g->h_small + 1, sizeof(double));
+    if (!(smax > 0)) return fail(WB_ENONFINITE, "no positive signal speed in the state");
+    *dt_out = cfl / smax;
+    return WB_OK;
+}
+
+int wb_conserved_totals(wb_grid* g, double out[8]) {
+    g_err.clear();
+    if (!g || !out) return fail(WB_EINVAL, "null argument");
+    WB_CK(cudaSetDevice(g->device));
+    double* res = g->d_partial + kPartials * 8;
+    int rc = enqueue_totals(g);
+    if (rc != WB_OK) return rc;
+    WB_CK(cudaMemcpyAsync(g->h_small + 2, res, sizeof(double) * 8, cudaMemcpyDeviceToHost, g->stream));
+    rc = check_flag(g);
+    if (rc != WB_OK) return rc;
+    std::memcpy(out, g->h_small + 2, sizeof(double) * 8);
+    return WB_OK;
+}
+
+int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    WB_CK(cudaSetDevice(g->device));
+    const long long N = g->N;
+    double* dU = U_out ? g->d_io : nullptr;
+    double* db = b_out ? g->d_io + 8 * N : nullptr;
+    if (g->precision == WB_FP64)
+        WB_CK(wb::launch_export<double>(static_cast<const double*>(g->un), dU, db, g->d_blocks,
+                                        g->d_patches, N, g->nblocks, g->stream));
+    else
+        WB_CK(wb::launch_export<float>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
+                                       g->d_patches, N, g->nblocks, g->stream));
+    if (U_out)
+        WB_CK(cudaMemcpyAsync(U_out, dU, sizeof(double) * 8 * N, cudaMemcpyDeviceToHost, g->stream));
+    if (b_out)
+        WB_CK(cudaMemcpyAsync(b_out, db, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, g->stream));
+    return check_flag(g);
+}
+
+int wb_sync(wb_grid* g) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    WB_CK(cudaSetDevice(g->device));
+    return check_flag(g);
+}
+
+int wb_get_info(wb_grid* g, wb_grid_info* info) {
+    g_err.clear();
+    if (!g || !info) return fail(WB_EINVAL, "null argument");
+    WB_CK(cudaSetDevice(g->device));
+    WB_CK(cudaMemcpyAsync(g->h_small, g->d_scalars, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                          g->stream));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    info->npatch = g->npatch;
+    info->ncells = g->N;
+    info->precision = g->precision;
+    info->integrator = g->integrator;
+    info->emf_mode = g->emf_mode;
+    info->device_bytes = g->bytes;
+    info->time = g->h_small[1];
+    info->steps = g->steps;
+    return WB_OK;
+}
+
+int wb_destroy(wb_grid* g) {
+    g_err.clear();
+    release(g);
+    return WB_OK;
+}
+
+}  // extern "C"

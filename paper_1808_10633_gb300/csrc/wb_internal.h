@@ -1,0 +1,92 @@
+// wb_internal.h -- types shared by the CUDA translation units of the library
+// (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace wb {
+
+// One periodic patch of the world grid (Sec. 2.2 "patches"); a single grid
+// is one patch.  Field f of the state lives at base + f*ncells + off + local.
+struct PatchDev {
+    int nx, ny, nz, pad;
+    long long off;
+};
+
+// Sweep tile: x = patch, y = start along the sweep axis, z = start along the
+// pencil axis, w = fixed third coordinate.
+using Tile = int4;
+
+// Cell block for the per-cell kernels: x = patch, y = first local cell.
+using CellBlock = int2;
+
+constexpr int kCellBlock = 256;   // cells per block of the per-cell kernels
+
+// Number of state arrays: rho, mx, my, mz, E (cell) + bx, by, bz (faces).
+constexpr int kNState = 8;
+// Stored flux components per axis: rho, mx, my, mz, E, B_t1, B_t2.
+constexpr int kNFlux = 7;
+
+template <class T>
+struct SweepArgs {
+    const T* __restrict__ src;     // state base (kNState arrays)
+    T* __restrict__ flux;          // flux base of this axis (kNFlux arrays)
+    T* __restrict__ er;            // cell -v x B (3 arrays) or nullptr
+    const Tile* __restrict__ tiles;
+    const PatchDev* __restrict__ patches;
+    long long ncells;              // stride between arrays
+    double gamma;
+};
+
+template <class T>
+struct UpdateArgs {
+    const T* un;                   // state at t^n (may alias dst)
+    const T* uk;                   // stage state the fluxes were taken from (may alias dst)
+    T* dst;                        // output stage state (may alias uk or un)
+    T* acc;                        // RK4 accumulator (may be null)
+    const T* __restrict__ flux;    // 3 axes x kNFlux arrays
+    const T* __restrict__ er;      // 3 arrays (emf_mode 0) or nullptr
+    const CellBlock* __restrict__ blocks;
+    const PatchDev* __restrict__ patches;
+    const double* __restrict__ dt; // device scalar
+    long long ncells;
+    double idx, idy, idz;
+    int stage;                     // SSP-RK3: 0,1,2; RK4: 0..3
+    int integrator;
+    int emf_mode;
+};
+
+// ---- launchers (one per translation unit) ---------------------------------
+template <class T>
+cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s);
+template <class T>
+cudaError_t prepare_sweep_kernels();
+void sweep_tile_shape(int axis, int* ta, int* tp);
+
+template <class T>
+cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
+
+template <class T>
+cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
+                       long long ncells, int nblocks, double idx, double idy, double idz,
+                       double gamma, unsigned long long* smax_bits, unsigned int* flag,
+                       cudaStream_t s);
+cudaError_t launch_set_dt(const unsigned long long* smax_bits, double cfl, double fixed_dt,
+                          double* dt, double* time, cudaStream_t s);
+
+template <class T>
+cudaError_t launch_totals(const T* state, const PatchDev* patches, int npatch,
+                          long long ncells, double* partial, int npartial,
+                          double dV, double* out, cudaStream_t s);
+
+template <class T>
+cudaError_t launch_import(const double* U, const double* b, T* state,
+                          const CellBlock* blocks, const PatchDev* patches,
+                          long long ncells, int nblocks, cudaStream_t s);
+template <class T>
+cudaError_t launch_export(const T* state, double* U, double* b,
+                          const CellBlock* blocks, const PatchDev* patches,
+                          long long ncells, int nblocks, cudaStream_t s);
+
+}  // namespace wb

@@ -1,0 +1,270 @@
+// wb_reduce.cu -- CFL time step (FP64 max reduction with warp shuffles),
+// deterministic FP64 conserved totals, and the FP64 <-> state conversions
+// used at the ABI.
+#include "wb_internal.h"
+
+#include <cfloat>
+
+namespace wb {
+namespace {
+
+__device__ __forceinline__ int inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+
+// dt rule: s = sum_d (|v_d| + c_f,d) / dx_d per cell, maximised over cells;
+// the fast speed along d uses B_d as the normal field.  All in FP64.
+template <class T>
+__global__ void __launch_bounds__(kCellBlock)
+cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
+           const PatchDev* __restrict__ patches, long long N, double idx, double idy,
+           double idz, double gamma, unsigned long long* smax_bits, unsigned int* flag) {
+    const CellBlock cb = blocks[blockIdx.x];
+    const PatchDev P = patches[cb.x];
+    const int local = cb.y + threadIdx.x;
+    const int nxy = P.nx * P.ny;
+    double s = 0.0;
+    if (local < nxy * P.nz) {
+        const int k = local / nxy;
+        const int rem = local - k * nxy;
+        const int j = rem / P.nx;
+        const int i = rem - j * P.nx;
+        const long long c = P.off + local;
+        const long long cx = c + (inc(i, P.nx) - i);
+        const long long cy = c + (long long)(inc(j, P.ny) - j) * P.nx;
+        const long long cz = c + (long long)(inc(k, P.nz) - k) * nxy;
+        const double rho = q[c];
+        const double v[3] = {double(q[N + c]) / rho, double(q[2 * N + c]) / rho,
+                             double(q[3 * N + c]) / rho};
+        const double B[3] = {0.5 * (double(q[5 * N + c]) + double(q[5 * N + cx])),
+                             0.5 * (double(q[6 * N + c]) + double(q[6 * N + cy])),
+                             0.5 * (double(q[7 * N + c]) + double(q[7 * N + cz]))};
+        const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const double kin = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double p = (gamma - 1.0) * (double(q[4 * N + c]) - kin - 0.5 * bb);
+        const double a2 = gamma * p / rho;
+        const double b2 = bb / rho;
+        const double sum = a2 + b2;
+        const double id[3] = {idx, idy, idz};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double ca2 = B[d] * B[d] / rho;
+            double disc = sum * sum - 4.0 * a2 * ca2;
+            disc = disc > 0.0 ? disc : 0.0;
+            const double cf = sqrt(0.5 * (sum + sqrt(disc)));
+            s += (fabs(v[d]) + cf) * id[d];
+        }
+        unsigned int bad = 0;
+        if (!(s <= DBL_MAX)) bad |= 1u;              // NaN or Inf
+        if (!(rho > 0.0) || !(p > 0.0)) bad |= 2u;
+        if (bad) {
+            atomicOr(flag, bad);
+            s = 0.0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    __shared__ double red[kCellBlock / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < kCellBlock / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        // s >= 0: the IEEE bit patterns order like the values
+        if (threadIdx.x == 0) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(s));
+    }
+}
+
+__global__ void set_dt_kernel(const unsigned long long* smax_bits, double cfl, double fixed_dt,
+                              double* dt, double* time) {
+    double d = fixed_dt;
+    if (!(fixed_dt > 0.0)) {
+        const double smax = __longlong_as_double((long long)*smax_bits);
+        d = smax > 0.0 ? cfl / smax : 0.0;
+    }
+    *dt = d;
+    *time += d;
+}
+
+// Totals: sum over cells of rho, m, E and of the face fields (for a periodic
+// patch the sum of the face means equals the sum over faces).  Pass 1: each
+// block reduces a fixed contiguous chunk in a fixed order; pass 2: one block
+// reduces the partials.  Same order on every call, so bitwise repeatable.
+template <class T>
+__global__ void __launch_bounds__(256)
+totals_pass1(const T* __restrict__ q, long long N, long long chunk, double* __restrict__ partial) {
+    const long long beg = (long long)blockIdx.x * chunk;
+    long long end = beg + chunk;
+    if (end > N) end = N;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long c = beg + threadIdx.x; c < end; c += 256) {
+#pragma unroll
+        for (int f = 0; f < 8; f++) acc[f] += double(q[f * N + c]);
+    }
+    __shared__ double red[8][256];
+#pragma unroll
+    for (int f = 0; f < 8; f++) red[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int f = 0; f < 8; f++) red[f][threadIdx.x] += red[f][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partial[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256)
+totals_pass2(const double* __restrict__ partial, int npartial, double dV, double* __restrict__ out) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < npartial; b += 256) {
+#pragma unroll
+        for (int f = 0; f < 8; f++) acc[f] += partial[b * 8 + f];
+    }
+    __shared__ double red[8][256];
+#pragma unroll
+    for (int f = 0; f < 8; f++) red[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int f = 0; f < 8; f++) red[f][threadIdx.x] += red[f][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // state order rho, mx, my, mz, E, bx, by, bz -> ABI order
+        // rho, mx, my, mz, Bx, By, Bz, E
+        out[0] = red[0][0] * dV;
+        out[1] = red[1][0] * dV;
+        out[2] = red[2][0] * dV;
+        out[3] = red[3][0] * dV;
+        out[4] = red[5][0] * dV;
+        out[5] = red[6][0] * dV;
+        out[6] = red[7][0] * dV;
+        out[7] = red[4][0] * dV;
+    }
+}
+
+// ABI layout (FP64): U[patch][8][cells] with (rho, mx, my, mz, Bx, By, Bz, E),
+// b[patch][3][cells]; state layout: field-major over all patches.
+template <class T>
+__global__ void __launch_bounds__(kCellBlock)
+import_kernel(const double* __restrict__ U, const double* __restrict__ b, T* __restrict__ q,
+              const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
+              long long N) {
+    const CellBlock cb = blocks[blockIdx.x];
+    const PatchDev P = patches[cb.x];
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    const int local = cb.y + threadIdx.x;
+    if (local >= np) return;
+    const long long c = P.off + local;
+    const double* u = U + 8 * P.off + local;
+    const double* bb = b + 3 * P.off + local;
+    q[c] = T(u[0]);
+    q[N + c] = T(u[np]);
+    q[2 * N + c] = T(u[2 * np]);
+    q[3 * N + c] = T(u[3 * np]);
+    q[4 * N + c] = T(u[7 * np]);
+    q[5 * N + c] = T(bb[0]);
+    q[6 * N + c] = T(bb[np]);
+    q[7 * N + c] = T(bb[2 * np]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kCellBlock)
+export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restrict__ b,
+              const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
+              long long N) {
+    const CellBlock cb = blocks[blockIdx.x];
+    const PatchDev P = patches[cb.x];
+    const int nxy = P.nx * P.ny;
+    const long long np = (long long)nxy * P.nz;
+    const int local = cb.y + threadIdx.x;
+    if (local >= np) return;
+    const int k = local / nxy;
+    const int rem = local - k * nxy;
+    const int j = rem / P.nx;
+    const int i = rem - j * P.nx;
+    const long long c = P.off + local;
+    const long long cx = c + (inc(i, P.nx) - i);
+    const long long cy = c + (long long)(inc(j, P.ny) - j) * P.nx;
+    const long long cz = c + (long long)(inc(k, P.nz) - k) * nxy;
+    if (U) {
+        double* u = U + 8 * P.off + local;
+        u[0] = double(q[c]);
+        u[np] = double(q[N + c]);
+        u[2 * np] = double(q[2 * N + c]);
+        u[3 * np] = double(q[3 * N + c]);
+        u[4 * np] = 0.5 * (double(q[5 * N + c]) + double(q[5 * N + cx]));
+        u[5 * np] = 0.5 * (double(q[6 * N + c]) + double(q[6 * N + cy]));
+        u[6 * np] = 0.5 * (double(q[7 * N + c]) + double(q[7 * N + cz]));
+        u[7 * np] = double(q[4 * N + c]);
+    }
+    if (b) {
+        double* o = b + 3 * P.off + local;
+        o[0] = double(q[5 * N + c]);
+        o[np] = double(q[6 * N + c]);
+        o[2 * np] = double(q[7 * N + c]);
+    }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
+                       long long ncells, int nblocks, double idx, double idy, double idz,
+                       double gamma, unsigned long long* smax_bits, unsigned int* flag,
+                       cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    cfl_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, ncells, idx, idy, idz,
+                                                 gamma, smax_bits, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(const unsigned long long* smax_bits, double cfl, double fixed_dt,
+                          double* dt, double* time, cudaStream_t s) {
+    set_dt_kernel<<<1, 1, 0, s>>>(smax_bits, cfl, fixed_dt, dt, time);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_totals(const T* state, const PatchDev*, int, long long ncells,
+                          double* partial, int npartial, double dV, double* out, cudaStream_t s) {
+    const long long chunk = (ncells + npartial - 1) / npartial;
+    totals_pass1<T><<<npartial, 256, 0, s>>>(state, ncells, chunk, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    totals_pass2<<<1, 256, 0, s>>>(partial, npartial, dV, out);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_import(const double* U, const double* b, T* state, const CellBlock* blocks,
+                          const PatchDev* patches, long long ncells, int nblocks, cudaStream_t s) {
+    import_kernel<T><<<nblocks, kCellBlock, 0, s>>>(U, b, state, blocks, patches, ncells);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock* blocks,
+                          const PatchDev* patches, long long ncells, int nblocks, cudaStream_t s) {
+    export_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, ncells);
+    return cudaGetLastError();
+}
+
+#define WB_INST(T)                                                                            \
+    template cudaError_t launch_cfl<T>(const T*, const CellBlock*, const PatchDev*, long long, \
+                                       int, double, double, double, double,                  \
+                                       unsigned long long*, unsigned int*, cudaStream_t);     \
+    template cudaError_t launch_totals<T>(const T*, const PatchDev*, int, long long, double*, \
+                                          int, double, double*, cudaStream_t);                \
+    template cudaError_t launch_import<T>(const double*, const double*, T*, const CellBlock*, \
+                                          const PatchDev*, long long, int, cudaStream_t);     \
+    template cudaError_t launch_export<T>(const T*, double*, double*, const CellBlock*,       \
+                                          const PatchDev*, long long, int, cudaStream_t);
+WB_INST(float)
+WB_INST(double)
+#undef WB_INST
+
+}  // namespace wb

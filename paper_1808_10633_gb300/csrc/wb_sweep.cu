@@ -1,0 +1,558 @@
+// wb_sweep.cu -- characteristic WENO5 flux sweeps (Donnert et al. 2018,
+// Sec. 2.1 eq. FWENO; Sec. 2.2 dimension-by-dimension sweeps).
+//
+// One thread computes the numerical flux through one interface.  A block
+// owns a 2-D slab of interfaces: TA along the sweep axis times TP pencils.
+// The TA+5 cells each pencil needs (3 below, 2 above the slab) are staged
+// once in shared memory with everything the interface step reads per cell:
+// the rotated conserved 7-vector, its physical flux, the seven |lambda| and
+// the primitives used by the interface average.  The sweep never moves the
+// grid ("rotation" of Sec. 2.2 is an index mapping): for the x sweep the
+// thread's x index walks the axis, for y and z the thread's x index walks
+// the pencils, so every global load and store is x-contiguous.
+//
+// Per interface (cells i-2..i+3 of the stencil):
+//   1. interface state = mean of the primitives of cells i, i+1;
+//   2. closed-form 7-wave eigensystem (Roe-Balsara normalisation) at it;
+//   3. projection of U_k, F_k on the left eigenvectors, done as
+//      (dW/dU) x followed by the sparse left vectors, in two groups of
+//      characteristic fields (fast+slow, then Alfven+entropy) so that the
+//      projected stencil fits in registers in FP64 too;
+//   4. local Lax-Friedrichs splitting, alpha_s = max |lambda_s| over the
+//      stencil and the interface state;
+//   5. WENO5-JS weights and phi_N for both split fluxes;
+//   6. back-projection (dU/dW applied to the primitive right vectors) plus
+//      the fourth-order central flux (-F_{i-1} + 7F_i + 7F_{i+1} - F_{i+2})/12.
+// The flux is written in global component order (rho, mx, my, mz, E,
+// B_t1, B_t2) to the face array of the lower face of cell i+1.
+#include "wb_internal.h"
+
+namespace wb {
+namespace {
+
+// ---- shared-memory slots per staged cell ----------------------------------
+enum : int {
+    SU = 0,      // U7: rho, m_n, m_t1, m_t2, B_t1, B_t2, E        (0..6)
+    SF = 7,      // F7 in the same order                           (7..13)
+    SL = 14,     // |lambda_s|, s = 0..6                           (14..20)
+    SP_U = 21, SP_V1, SP_V2, SP_BN, SP_P,   // primitives for the mean
+    kNSlot = 26
+};
+
+template <class T> __device__ __forceinline__ T sq_root(T x);
+template <> __device__ __forceinline__ float sq_root<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sq_root<double>(double x) { return sqrt(x); }
+
+template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <class T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// Sec. 2.1: phi_N(a,b,c,d) = 1/3 w0 (a-2b+c) + 1/6 (w2-1/2)(b-2c+d) with
+// IS_0..2 as printed, alpha_k = d_k/(eps+IS_k)^2, d = (1, 6, 3), eps = 1e-6.
+__device__ __forceinline__ double phi_n(double a, double b, double c, double d) {
+    const double eps = 1e-6;
+    double t0 = a - b, t1 = a - 3.0 * b;
+    double is0 = 13.0 * t0 * t0 + 3.0 * t1 * t1;
+    double t2 = b - c, t3 = b + c;
+    double is1 = 13.0 * t2 * t2 + 3.0 * t3 * t3;
+    double t4 = c - d, t5 = 3.0 * c - d;
+    double is2 = 13.0 * t4 * t4 + 3.0 * t5 * t5;
+    double e0 = eps + is0, e1 = eps + is1, e2 = eps + is2;
+    e0 *= e0; e1 *= e1; e2 *= e2;
+    // omega_k = (d_k / e_k) / sum_j (d_j / e_j): one division in FP64
+    double n0 = e1 * e2, n2 = 3.0 * e0 * e1;
+    double r = 1.0 / (n0 + 6.0 * e0 * e2 + n2);
+    double w0 = n0 * r, w2 = n2 * r;
+    return w0 * (a - 2.0 * b + c) * (1.0 / 3.0) + (w2 - 0.5) * (b - 2.0 * c + d) * (1.0 / 6.0);
+}
+
+__device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
+    const float eps = 1e-6f;
+    float t0 = a - b, t1 = a - 3.0f * b;
+    float is0 = 13.0f * t0 * t0 + 3.0f * t1 * t1;
+    float t2 = b - c, t3 = b + c;
+    float is1 = 13.0f * t2 * t2 + 3.0f * t3 * t3;
+    float t4 = c - d, t5 = 3.0f * c - d;
+    float is2 = 13.0f * t4 * t4 + 3.0f * t5 * t5;
+    float e0 = eps + is0, e1 = eps + is1, e2 = eps + is2;
+    // reciprocals keep the FP32 range: (eps+IS)^2 products could overflow
+    float a0 = 1.0f / (e0 * e0), a1 = 6.0f / (e1 * e1), a2 = 3.0f / (e2 * e2);
+    float r = 1.0f / (a0 + a1 + a2);
+    float w0 = a0 * r, w2 = a2 * r;
+    return w0 * (a - 2.0f * b + c) * (1.0f / 3.0f) + (w2 - 0.5f) * (b - 2.0f * c + d) * (1.0f / 6.0f);
+}
+
+// Correction of eq. FWENO for one characteristic field:
+// -phi_N(D+_{i-3/2}, D+_{i-1/2}, D+_{i+1/2}, D+_{i+3/2})
+// +phi_N(D-_{i+5/2}, D-_{i+3/2}, D-_{i+1/2}, D-_{i-1/2}),
+// D+-_{k+1/2} = g+-_{k+1} - g+-_k, g+- = (g +- alpha w)/2.
+template <class T>
+__device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha) {
+    const T ha = T(0.5) * alpha;
+    T gp[5], gm[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) gp[k] = T(0.5) * g[k] + ha * w[k];
+#pragma unroll
+    for (int k = 0; k < 5; k++) gm[k] = T(0.5) * g[k + 1] - ha * w[k + 1];
+    // gm[k] holds g-_{k+1}
+    T dp0 = gp[1] - gp[0], dp1 = gp[2] - gp[1], dp2 = gp[3] - gp[2], dp3 = gp[4] - gp[3];
+    T dm1 = gm[1] - gm[0], dm2 = gm[2] - gm[1], dm3 = gm[3] - gm[2], dm4 = gm[4] - gm[3];
+    return phi_n(dm4, dm3, dm2, dm1) - phi_n(dp0, dp1, dp2, dp3);
+}
+
+// Interface eigen-structure: everything the projection and back-projection
+// need, with 1/rho and (gamma-1) folded into the left coefficients.
+template <class T>
+struct Eig {
+    T rho, u, v1, v2, b1, b2, hv2, gm1;
+    T be1, be2, S;
+    T alf, als, cf, cs, a, sr, a2;
+    T Af, Bf, Cf, Df, As, Bs, Cs, Ds, Aa, Ba, Ee;
+    T lam[7];
+};
+
+// beta and (alpha_f, alpha_s) with the degeneracy rules; FP64 throughout.
+__device__ __forceinline__ void degenerate_rules(double rho, double bn, double b1, double b2,
+                                                 double p, double gamma,
+                                                 double& be1, double& be2,
+                                                 double& alf, double& als,
+                                                 double& cf2o, double& cs2o) {
+    double bp2 = b1 * b1 + b2 * b2;
+    double bt2 = bn * bn + bp2;
+    if (bp2 > 1e-24 * (bt2 > 1.0 ? bt2 : 1.0)) {
+        double bp = sqrt(bp2);
+        be1 = b1 / bp;
+        be2 = b2 / bp;
+    } else {
+        be1 = be2 = 0.70710678118654752440;
+    }
+    double a2 = gamma * p / rho;
+    double ca2 = bn * bn / rho;
+    double b2r = bt2 / rho;
+    double s = a2 + b2r;
+    double disc = s * s - 4.0 * a2 * ca2;
+    disc = disc > 0.0 ? disc : 0.0;
+    double q = sqrt(disc);
+    double cf2 = 0.5 * (s + q);
+    double cs2 = 0.5 * (s - q);
+    cs2 = cs2 > 0.0 ? cs2 : 0.0;
+    if (cf2 - cs2 <= 1e-12 * (a2 + b2r)) {
+        if (a2 >= ca2) { alf = 1.0; als = 0.0; } else { alf = 0.0; als = 1.0; }
+    } else {
+        double r = 1.0 / (cf2 - cs2);
+        double t1 = (a2 - cs2) * r, t2 = (cf2 - a2) * r;
+        alf = sqrt(t1 > 0.0 ? t1 : 0.0);
+        als = sqrt(t2 > 0.0 ? t2 : 0.0);
+    }
+    cf2o = cf2;
+    cs2o = cs2;
+}
+
+template <class T>
+__device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, T p, T gamma,
+                                      Eig<T>& e) {
+    const T rinv = T(1) / rho;
+    const T a2 = gamma * p * rinv;
+    const T ca2 = bn * bn * rinv;
+    T cf2, cs2, be1, be2, alf, als;
+    if constexpr (sizeof(T) == 8) {
+        double dbe1, dbe2, dalf, dals, dcf2, dcs2;
+        degenerate_rules(rho, bn, b1, b2, p, gamma, dbe1, dbe2, dalf, dals, dcf2, dcs2);
+        be1 = T(dbe1); be2 = T(dbe2); alf = T(dalf); als = T(dals);
+        cf2 = T(dcf2); cs2 = T(dcs2);
+    } else {
+        // FP32 bulk; the normalisation near B_perp -> 0 and near cf = cs
+        // (fast/slow/Alfven coincidence) is taken in FP64.
+        const T bp2 = b1 * b1 + b2 * b2;
+        const T bt2 = bn * bn + bp2;
+        const T b2r = bt2 * rinv;
+        const T s = a2 + b2r;
+        T disc = s * s - T(4) * a2 * ca2;
+        disc = tmax(disc, T(0));
+        const T q = sq_root(disc);
+        cf2 = T(0.5) * (s + q);
+        cs2 = tmax(T(0.5) * (s - q), T(0));
+        const bool near_bperp = !(bp2 > T(1e-6) * bt2);
+        const bool near_triple = !(cf2 - cs2 > T(1e-3) * (a2 + b2r));
+        if (near_bperp || near_triple) {
+            double dbe1, dbe2, dalf, dals, dcf2, dcs2;
+            degenerate_rules(rho, bn, b1, b2, p, gamma, dbe1, dbe2, dalf, dals, dcf2, dcs2);
+            be1 = T(dbe1); be2 = T(dbe2); alf = T(dalf); als = T(dals);
+            cf2 = T(dcf2); cs2 = T(dcs2);
+        } else {
+            const T bp = sq_root(bp2);
+            be1 = b1 / bp;
+            be2 = b2 / bp;
+            const T r = T(1) / (cf2 - cs2);
+            alf = sq_root(tmax((a2 - cs2) * r, T(0)));
+            als = sq_root(tmax((cf2 - a2) * r, T(0)));
+        }
+    }
+    const T cf = sq_root(cf2), cs = sq_root(cs2), ca = sq_root(ca2);
+    const T a = sq_root(a2), sr = sq_root(rho);
+    const T S = bn >= T(0) ? T(1) : T(-1);
+    const T gm1 = gamma - T(1);
+    const T X = alf * alf * cf2 + als * als * cs2;
+    const T hXr = T(0.5) / X * rinv;
+    const T isr = T(1) / sr;
+    const T hia = T(0.5) / a * isr;          // 1 / (2 a sqrt(rho))
+    const T hgp = T(0.5) * gm1 / (gamma * p); // (gamma-1) / (2 rho a^2)
+    e.rho = rho; e.u = u; e.v1 = v1; e.v2 = v2; e.b1 = b1; e.b2 = b2;
+    e.hv2 = T(0.5) * (u * u + v1 * v1 + v2 * v2);
+    e.gm1 = gm1;
+    e.be1 = be1; e.be2 = be2; e.S = S;
+    e.alf = alf; e.als = als; e.cf = cf; e.cs = cs; e.a = a; e.sr = sr; e.a2 = a2;
+    e.Af = alf * cf * hXr;
+    e.Bf = -als * cs * S * hXr;
+    e.Cf = als * hia;
+    e.Df = alf * hgp;
+    e.As = als * cs * hXr;
+    e.Bs = alf * cf * S * hXr;
+    e.Cs = -alf * hia;
+    e.Ds = als * hgp;
+    e.Aa = T(0.5) * rinv;
+    e.Ba = T(0.5) * S * isr;
+    e.Ee = gm1 / a2;
+    e.lam[0] = tabs(u - cf); e.lam[1] = tabs(u - ca); e.lam[2] = tabs(u - cs);
+    e.lam[3] = tabs(u);
+    e.lam[4] = tabs(u + cs); e.lam[5] = tabs(u + ca); e.lam[6] = tabs(u + cf);
+}
+
+// ---- staging --------------------------------------------------------------
+// Per cell: cell B from the faces, rotation into the (n, t1, t2) frame,
+// primitives, the physical flux along n, the seven |lambda| and, in the x
+// sweep, the cell value of -v x B for the constrained-transport EMFs.
+template <class T, int AXIS>
+__device__ __forceinline__ void stage_cell(const SweepArgs<T>& A, const PatchDev& P,
+                                           int i, int j, int k, T* __restrict__ sm,
+                                           int nc, int idx, bool write_er) {
+    const long long N = A.ncells;
+    const T* __restrict__ q = A.src;
+    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
+    const int ip = (i + 1 == P.nx) ? 0 : i + 1;
+    const int jp = (j + 1 == P.ny) ? 0 : j + 1;
+    const int kp = (k + 1 == P.nz) ? 0 : k + 1;
+    const long long cxp = c + (ip - i);
+    const long long cyp = c + (long long)(jp - j) * P.nx;
+    const long long czp = c + (long long)(kp - k) * P.nx * P.ny;
+    const T rho = q[c], mx = q[N + c], my = q[2 * N + c], mz = q[3 * N + c], E = q[4 * N + c];
+    const T Bx = T(0.5) * (q[5 * N + c] + q[5 * N + cxp]);
+    const T By = T(0.5) * (q[6 * N + c] + q[6 * N + cyp]);
+    const T Bz = T(0.5) * (q[7 * N + c] + q[7 * N + czp]);
+    T mn, m1, m2, bn, b1, b2;
+    if (AXIS == 0) { mn = mx; m1 = my; m2 = mz; bn = Bx; b1 = By; b2 = Bz; }
+    else if (AXIS == 1) { mn = my; m1 = mz; m2 = mx; bn = By; b1 = Bz; b2 = Bx; }
+    else { mn = mz; m1 = mx; m2 = my; bn = Bz; b1 = Bx; b2 = By; }
+    const T g = T(A.gamma);
+    const T rinv = T(1) / rho;
+    const T u = mn * rinv, v1 = m1 * rinv, v2 = m2 * rinv;
+    const T bb = bn * bn + b1 * b1 + b2 * b2;
+    const T kin = T(0.5) * (mn * u + m1 * v1 + m2 * v2);
+    const T p = (g - T(1)) * (E - kin - T(0.5) * bb);
+    const T pt = p + T(0.5) * bb;
+    const T vb = u * bn + v1 * b1 + v2 * b2;
+    sm[(SU + 0) * nc + idx] = rho;
+    sm[(SU + 1) * nc + idx] = mn;
+    sm[(SU + 2) * nc + idx] = m1;
+    sm[(SU + 3) * nc + idx] = m2;
+    sm[(SU + 4) * nc + idx] = b1;
+    sm[(SU + 5) * nc + idx] = b2;
+    sm[(SU + 6) * nc + idx] = E;
+    sm[(SF + 0) * nc + idx] = mn;
+    sm[(SF + 1) * nc + idx] = mn * u + pt - bn * bn;
+    sm[(SF + 2) * nc + idx] = m1 * u - bn * b1;
+    sm[(SF + 3) * nc + idx] = m2 * u - bn * b2;
+    sm[(SF + 4) * nc + idx] = u * b1 - v1 * bn;
+    sm[(SF + 5) * nc + idx] = u * b2 - v2 * bn;
+    sm[(SF + 6) * nc + idx] = (E + pt) * u - bn * vb;
+    const T a2 = g * p * rinv;
+    const T ca2 = bn * bn * rinv;
+    const T s = a2 + bb * rinv;
+    T disc = s * s - T(4) * a2 * ca2;
+    disc = tmax(disc, T(0));
+    const T qd = sq_root(disc);
+    const T cf = sq_root(T(0.5) * (s + qd));
+    const T cs = sq_root(tmax(T(0.5) * (s - qd), T(0)));
+    const T ca = sq_root(ca2);
+    sm[(SL + 0) * nc + idx] = tabs(u - cf);
+    sm[(SL + 1) * nc + idx] = tabs(u - ca);
+    sm[(SL + 2) * nc + idx] = tabs(u - cs);
+    sm[(SL + 3) * nc + idx] = tabs(u);
+    sm[(SL + 4) * nc + idx] = tabs(u + cs);
+    sm[(SL + 5) * nc + idx] = tabs(u + ca);
+    sm[(SL + 6) * nc + idx] = tabs(u + cf);
+    sm[SP_U * nc + idx] = u;
+    sm[SP_V1 * nc + idx] = v1;
+    sm[SP_V2 * nc + idx] = v2;
+    sm[SP_BN * nc + idx] = bn;
+    sm[SP_P * nc + idx] = p;
+    if (AXIS == 0 && write_er) {
+        // -v x B in the global frame (x sweep: u = vx, v1 = vy, v2 = vz)
+        A.er[c] = v2 * b1 - v1 * b2;
+        A.er[N + c] = u * b2 - v2 * bn;
+        A.er[2 * N + c] = v1 * bn - u * b1;
+    }
+}
+
+// ---- one interface ----------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void load7(const T* __restrict__ sm, int nc, int base, int idx, T (&x)[7]) {
+#pragma unroll
+    for (int f = 0; f < 7; f++) x[f] = sm[(base + f) * nc + idx];
+}
+
+// first projection group: fast-, slow-, slow+, fast+ (s = 0, 2, 4, 6)
+template <class T>
+__device__ __forceinline__ void project_fs(const Eig<T>& e, const T (&x)[7], T (&o)[4]) {
+    const T du = x[1] - e.u * x[0];
+    const T dv1 = x[2] - e.v1 * x[0];
+    const T dv2 = x[3] - e.v2 * x[0];
+    const T P = x[6] + e.hv2 * x[0] - e.u * x[1] - e.v1 * x[2] - e.v2 * x[3]
+              - e.b1 * x[4] - e.b2 * x[5];
+    const T vpar = e.be1 * dv1 + e.be2 * dv2;
+    const T bpar = e.be1 * x[4] + e.be2 * x[5];
+    const T tf1 = e.Af * du + e.Bf * vpar, tf2 = e.Cf * bpar + e.Df * P;
+    const T ts1 = e.As * du + e.Bs * vpar, ts2 = e.Cs * bpar + e.Ds * P;
+    o[0] = tf2 - tf1;
+    o[1] = ts2 - ts1;
+    o[2] = ts2 + ts1;
+    o[3] = tf2 + tf1;
+}
+
+// second projection group: Alfven-, entropy, Alfven+ (s = 1, 3, 5)
+template <class T>
+__device__ __forceinline__ void project_ae(const Eig<T>& e, const T (&x)[7], T (&o)[3]) {
+    const T dv1 = x[2] - e.v1 * x[0];
+    const T dv2 = x[3] - e.v2 * x[0];
+    const T P = x[6] + e.hv2 * x[0] - e.u * x[1] - e.v1 * x[2] - e.v2 * x[3]
+              - e.b1 * x[4] - e.b2 * x[5];
+    const T vperp = e.be1 * dv2 - e.be2 * dv1;
+    const T bperp = e.be1 * x[5] - e.be2 * x[4];
+    const T t1 = e.Aa * vperp, t2 = e.Ba * bperp;
+    o[0] = t1 + t2;
+    o[1] = x[0] - e.Ee * P;
+    o[2] = t1 - t2;
+}
+
+template <class T>
+__device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const int (&id)[6],
+                                      int s, T lam_avg) {
+    T al = lam_avg;
+#pragma unroll
+    for (int m = 0; m < 6; m++) al = tmax(al, sm[(SL + s) * nc + id[m]]);
+    return al;
+}
+
+template <class T>
+__device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc, const int (&id)[6],
+                                               T gamma, T (&out)[7]) {
+    // 1-2. interface state and eigen-structure
+    Eig<T> e;
+    {
+        const int l = id[2], r = id[3];
+        const T h = T(0.5);
+        eigen<T>(h * (sm[SU * nc + l] + sm[SU * nc + r]),
+                 h * (sm[SP_U * nc + l] + sm[SP_U * nc + r]),
+                 h * (sm[SP_V1 * nc + l] + sm[SP_V1 * nc + r]),
+                 h * (sm[SP_V2 * nc + l] + sm[SP_V2 * nc + r]),
+                 h * (sm[SP_BN * nc + l] + sm[SP_BN * nc + r]),
+                 h * (sm[(SU + 4) * nc + l] + sm[(SU + 4) * nc + r]),
+                 h * (sm[(SU + 5) * nc + l] + sm[(SU + 5) * nc + r]),
+                 h * (sm[SP_P * nc + l] + sm[SP_P * nc + r]), gamma, e);
+    }
+    T corr[7];
+    // central flux (-F_{i-1} + 7F_i + 7F_{i+1} - F_{i+2}) / 12
+    {
+        T f1[7], f2[7], f3[7], f4[7];
+        load7(sm, nc, SF, id[1], f1);
+        load7(sm, nc, SF, id[2], f2);
+        load7(sm, nc, SF, id[3], f3);
+        load7(sm, nc, SF, id[4], f4);
+#pragma unroll
+        for (int f = 0; f < 7; f++)
+            out[f] = (T(7) * (f2[f] + f3[f]) - (f1[f] + f4[f])) * T(1.0 / 12.0);
+    }
+    // 3-5. fast and slow fields
+    {
+        T w[4][6], g[4][6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            T x[7], o[4];
+            load7(sm, nc, SU, id[m], x);
+            project_fs(e, x, o);
+#pragma unroll
+            for (int f = 0; f < 4; f++) w[f][m] = o[f];
+            load7(sm, nc, SF, id[m], x);
+            project_fs(e, x, o);
+#pragma unroll
+            for (int f = 0; f < 4; f++) g[f][m] = o[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+            const int s = 2 * f;
+            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, e.lam[s]));
+        }
+    }
+    // 3-5. Alfven and entropy fields
+    {
+        T w[3][6], g[3][6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            T x[7], o[3];
+            load7(sm, nc, SU, id[m], x);
+            project_ae(e, x, o);
+#pragma unroll
+            for (int f = 0; f < 3; f++) w[f][m] = o[f];
+            load7(sm, nc, SF, id[m], x);
+            project_ae(e, x, o);
+#pragma unroll
+            for (int f = 0; f < 3; f++) g[f][m] = o[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            const int s = 2 * f + 1;
+            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, e.lam[s]));
+        }
+    }
+    // 6. back-projection: sum_s r_s corr_s in primitive variables, then dU/dW
+    const T Fp = corr[6] + corr[0], Fm = corr[6] - corr[0];
+    const T Sp = corr[4] + corr[2], Sm = corr[4] - corr[2];
+    const T Ap = corr[5] + corr[1], Am = corr[5] - corr[1];
+    const T fs = e.alf * Fp + e.als * Sp;
+    const T drho = e.rho * fs + corr[3];
+    const T du = e.alf * e.cf * Fm + e.als * e.cs * Sm;
+    const T dvpar = e.S * (e.alf * e.cf * Sm - e.als * e.cs * Fm);
+    const T dvperp = Ap;
+    const T dbpar = e.a * e.sr * (e.als * Fp - e.alf * Sp);
+    const T dbperp = -e.S * e.sr * Am;
+    const T dp = e.rho * e.a2 * fs;
+    const T dv1 = e.be1 * dvpar - e.be2 * dvperp;
+    const T dv2 = e.be2 * dvpar + e.be1 * dvperp;
+    const T db1 = e.be1 * dbpar - e.be2 * dbperp;
+    const T db2 = e.be2 * dbpar + e.be1 * dbperp;
+    out[0] += drho;
+    out[1] += e.u * drho + e.rho * du;
+    out[2] += e.v1 * drho + e.rho * dv1;
+    out[3] += e.v2 * drho + e.rho * dv2;
+    out[4] += db1;
+    out[5] += db2;
+    out[6] += e.hv2 * drho + e.rho * (e.u * du + e.v1 * dv1 + e.v2 * dv2)
+            + e.b1 * db1 + e.b2 * db2 + dp / e.gm1;
+}
+
+// ---- the kernel -------------------------------------------------------------
+template <int AXIS> struct Shape;
+template <> struct Shape<0> { static constexpr int TA = 32, TP = 8; };
+template <> struct Shape<1> { static constexpr int TA = 8, TP = 32; };
+template <> struct Shape<2> { static constexpr int TA = 8, TP = 32; };
+
+template <class T, int AXIS>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
+    constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
+    constexpr int NS = TA + 5;
+    constexpr int NC = NS * TP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+
+    const Tile tile = A.tiles[blockIdx.x];
+    const PatchDev P = A.patches[tile.x];
+    const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
+    const int np = AXIS == 0 ? P.ny : P.nx;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+
+    // staging: cells tile.y-3 .. tile.y+TA+1 along the axis, TP pencils
+    for (int e = tid; e < NC; e += TA * TP) {
+        int s, tp;
+        if (AXIS == 0) { tp = e / NS; s = e - tp * NS; }
+        else { s = e / TP; tp = e - s * TP; }
+        const int cp = tile.z + tp;
+        if (cp >= np) continue;
+        const int raw = tile.y - 3 + s;
+        const int ca = wrap(raw, na);
+        int i, j, k;
+        if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
+        else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
+        else { i = cp; j = tile.w; k = ca; }
+        const bool own = raw >= tile.y && raw < tile.y + TA && raw < na;
+        const int idx = AXIS == 0 ? tp * NS + s : s * TP + tp;
+        stage_cell<T, AXIS>(A, P, i, j, k, sm, NC, idx, own && A.er != nullptr);
+    }
+    __syncthreads();
+
+    const int ta = AXIS == 0 ? threadIdx.x : threadIdx.y;
+    const int tp = AXIS == 0 ? threadIdx.y : threadIdx.x;
+    const int ia = tile.y + ta, ip = tile.z + tp;
+    if (ia >= na || ip >= np) return;
+    int id[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
+    T F[7];
+    interface_flux<T>(sm, NC, id, T(A.gamma), F);
+
+    // rotate back and store at the lower face of cell ia
+    int i, j, k;
+    if (AXIS == 0) { i = ia; j = ip; k = tile.w; }
+    else if (AXIS == 1) { i = ip; j = ia; k = tile.w; }
+    else { i = ip; j = tile.w; k = ia; }
+    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
+    const long long N = A.ncells;
+    T* __restrict__ fo = A.flux;
+    T fx, fy, fz;
+    if (AXIS == 0) { fx = F[1]; fy = F[2]; fz = F[3]; }
+    else if (AXIS == 1) { fy = F[1]; fz = F[2]; fx = F[3]; }
+    else { fz = F[1]; fx = F[2]; fy = F[3]; }
+    fo[c] = F[0];
+    fo[N + c] = fx;
+    fo[2 * N + c] = fy;
+    fo[3 * N + c] = fz;
+    fo[4 * N + c] = F[6];
+    fo[5 * N + c] = F[4];
+    fo[6 * N + c] = F[5];
+}
+
+template <class T, int AXIS>
+constexpr size_t smem_bytes() {
+    return sizeof(T) * kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP;
+}
+
+}  // namespace
+
+void sweep_tile_shape(int axis, int* ta, int* tp) {
+    if (axis == 0) { *ta = Shape<0>::TA; *tp = Shape<0>::TP; }
+    else if (axis == 1) { *ta = Shape<1>::TA; *tp = Shape<1>::TP; }
+    else { *ta = Shape<2>::TA; *tp = Shape<2>::TP; }
+}
+
+template <class T>
+cudaError_t prepare_sweep_kernels() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(sweep_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<T, 0>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<T, 1>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<T, 2>());
+}
+
+template <class T>
+cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const dim3 block(32, 8);
+    if (axis == 0) sweep_kernel<T, 0><<<ntiles, block, smem_bytes<T, 0>(), s>>>(a);
+    else if (axis == 1) sweep_kernel<T, 1><<<ntiles, block, smem_bytes<T, 1>(), s>>>(a);
+    else sweep_kernel<T, 2><<<ntiles, block, smem_bytes<T, 2>(), s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t prepare_sweep_kernels<float>();
+template cudaError_t prepare_sweep_kernels<double>();
+template cudaError_t launch_sweep<float>(int, const SweepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_sweep<double>(int, const SweepArgs<double>&, int, cudaStream_t);
+
+}  // namespace wb

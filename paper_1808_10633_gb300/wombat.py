@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libwombat_gb300.so (include/wombat_gb300.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  There is no CPU fallback; loading fails loudly when the library is
+missing.  Host arrays are numpy float64 arrays (pageable) or pinned torch
+tensors; the CUDA stream handle may come from torch.cuda.current_stream().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwombat_gb300.so")
+
+WB_OK, WB_EINVAL, WB_ECUDA, WB_ENOMEM, WB_ENONFINITE, WB_ETIMEOUT, WB_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+WB_FP64, WB_FP32 = 0, 1
+WB_SSPRK3, WB_RK4 = 0, 1
+PRECISIONS = {"fp64": WB_FP64, "fp32": WB_FP32}
+INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
+
+# every entry point declared in include/wombat_gb300.h
+EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
+           "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
+           "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak")
+KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals")
+
+
+class WombatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"wombat error {code}: {msg}")
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("npatch", ctypes.c_int), ("dims", ctypes.POINTER(ctypes.c_int)),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("ghost", ctypes.c_int), ("precision", ctypes.c_int),
+        ("integrator", ctypes.c_int), ("emf_mode", ctypes.c_int),
+    ]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [
+        ("npatch", ctypes.c_int), ("ncells", ctypes.c_longlong), ("precision", ctypes.c_int),
+        ("integrator", ctypes.c_int), ("emf_mode", ctypes.c_int),
+        ("device_bytes", ctypes.c_longlong), ("time", ctypes.c_double), ("steps", ctypes.c_longlong),
+    ]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree library (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+    L.wb_init_grid.argtypes = [ctypes.POINTER(GridDesc), vp, vp, vp, ctypes.POINTER(vp)]
+    L.wb_set_state.argtypes = [vp, vp, vp]
+    L.wb_step.argtypes = [vp, d, i]
+    L.wb_step_cfl.argtypes = [vp, d, i]
+    L.wb_cfl_dt.argtypes = [vp, d, dp]
+    L.wb_conserved_totals.argtypes = [vp, dp]
+    L.wb_get_state.argtypes = [vp, vp, vp]
+    L.wb_sync.argtypes = [vp]
+    L.wb_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
+    L.wb_destroy.argtypes = [vp]
+    L.wb_step_profiled.argtypes = [vp, d, i, i, dp, ctypes.POINTER(ctypes.c_int), dp]
+    L.wb_alu_peak.argtypes = [i, dp]
+    L.wb_last_error.restype = ctypes.c_char_p
+    L.wb_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("wb_last_error", "wb_version"):
+            getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != WB_OK:
+        raise WombatError(rc, load().wb_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Host pointer of a C-contiguous float64 numpy array or a pinned torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+        return a.ctypes.data
+    assert str(a.dtype) == "torch.float64" and a.is_contiguous() and not a.is_cuda
+    return a.data_ptr()
+
+
+class Grid:
+    """A set of periodic patches advanced by the CUDA library.
+
+    U: (npatch*8*cells) or (8, nz, ny, nx) float64 host array in the ABI
+    layout; b: faces (3, nz, ny, nx) or flat.  dims: list of (nx, ny, nz)."""
+
+    def __init__(self, dims: Sequence[Sequence[int]], dx, dy, dz, U, b, gamma=5.0 / 3.0,
+                 precision="fp64", integrator="ssprk3", emf_mode=0, stream=None):
+        L = load()
+        self._lib = L
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.ncells = sum(d[0] * d[1] * d[2] for d in self.dims)
+        flat = np.array([v for d in self.dims for v in d], dtype=np.int32)
+        self._dims = flat
+        desc = GridDesc(len(self.dims), flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        float(dx), float(dy), float(dz), float(gamma), 3,
+                        PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision,
+                        INTEGRATORS.get(integrator, integrator) if isinstance(integrator, str) else integrator,
+                        int(emf_mode))
+        self.precision = precision
+        U = self._host(U, 8)
+        b = self._host(b, 3)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(int(stream)) if stream else None
+        _check(L.wb_init_grid(ctypes.byref(desc), _ptr(U), _ptr(b), st, ctypes.byref(h)))
+        self._h = h
+
+    def _host(self, a, nf):
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            assert a.size == nf * self.ncells, (a.shape, nf, self.ncells)
+        return a
+
+    @classmethod
+    def from_state(cls, st, **kw):
+        nx, ny, nz = st.dims
+        b = np.stack([st.bx, st.by, st.bz])
+        return cls([(nx, ny, nz)], st.dx, st.dy, st.dz, st.U, b, gamma=st.gamma, **kw)
+
+    @classmethod
+    def from_patches(cls, states, **kw):
+        dims = [s.dims for s in states]
+        U = np.concatenate([s.U.ravel() for s in states])
+        b = np.concatenate([np.stack([s.bx, s.by, s.bz]).ravel() for s in states])
+        s0 = states[0]
+        return cls(dims, s0.dx, s0.dy, s0.dz, U, b, gamma=s0.gamma, **kw)
+
+    # -- calls -------------------------------------------------------------
+    def set_state(self, U, b):
+        _check(self._lib.wb_set_state(self._h, _ptr(self._host(U, 8)), _ptr(self._host(b, 3))))
+
+    def step(self, dt: float, nsteps: int = 1):
+        _check(self._lib.wb_step(self._h, float(dt), int(nsteps)))
+
+    def step_cfl(self, cfl: float = 0.4, nsteps: int = 1):
+        _check(self._lib.wb_step_cfl(self._h, float(cfl), int(nsteps)))
+
+    def step_profiled(self, cfl: float, nsteps: int, with_totals: bool = True):
+        """CFL steps with per-kernel CUDA-event timing on the grid's stream.
+        Returns (total_ms, {class: ms}, {class: launches})."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        cnt = (ctypes.c_int * len(KERNEL_CLASSES))()
+        tot = ctypes.c_double()
+        _check(self._lib.wb_step_profiled(self._h, float(cfl), int(nsteps), int(bool(with_totals)),
+                                          ms, cnt, ctypes.byref(tot)))
+        return (tot.value, dict(zip(KERNEL_CLASSES, ms[:])), dict(zip(KERNEL_CLASSES, cnt[:])))
+
+    def cfl_dt(self, cfl: float = 0.4) -> float:
+        out = ctypes.c_double()
+        _check(self._lib.wb_cfl_dt(self._h, float(cfl), ctypes.byref(out)))
+        return out.value
+
+    def totals(self) -> np.ndarray:
+        out = (ctypes.c_double * 8)()
+        _check(self._lib.wb_conserved_totals(self._h, out))
+        return np.array(out[:])
+
+    def get_state(self, U_out=None, b_out=None):
+        """Returns (U, b) as flat float64 arrays (or fills the given buffers)."""
+        U = np.empty(8 * self.ncells) if U_out is None else U_out
+        b = np.empty(3 * self.ncells) if b_out is None else b_out
+        _check(self._lib.wb_get_state(self._h, _ptr(U), _ptr(b)))
+        return U, b
+
+    def get_state_single(self):
+        """(U[8,nz,ny,nx], bx, by, bz) for a one-patch grid."""
+        nx, ny, nz = self.dims[0]
+        U, b = self.get_state()
+        b = b.reshape(3, nz, ny, nx)
+        return U.reshape(8, nz, ny, nx), b[0], b[1], b[2]
+
+    def sync(self):
+        _check(self._lib.wb_sync(self._h))
+
+    def info(self) -> dict:
+        inf = GridInfo()
+        _check(self._lib.wb_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in GridInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.wb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def version() -> str:
+    return load().wb_version().decode()
+
+
+def alu_peak_tflops(precision="fp32") -> float:
+    """Measured FMA throughput of the current GPU (TFLOP/s)."""
+    out = ctypes.c_double()
+    p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    _check(load().wb_alu_peak(p, ctypes.byref(out)))
+    return out.value

@@ -1,0 +1,179 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+Tolerances: FP64 must match the oracle to 1e-12 relative per step, with the
+relative error of a field taken as max|GPU - oracle| / max|oracle field|;
+a field that vanishes in exact arithmetic (e.g. m_x of the Alfven wave, made
+of round-off only) is measured against a floor of 1e-3 of the largest field
+of the state instead of its own noise.  The GPU sums
+differently ordered but algebraically identical expressions, so the
+expected mismatch is a few ulps times the condition of the WENO weights.
+FP32 runs are compared per field by L1 relative to the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1808_10633_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def wb():
+    from paper_1808_10633_gb300 import build, wombat
+
+    build.build()
+    return wombat
+
+
+def ogrid(orc, st, emf_mode=0):
+    nx, ny, nz = st.dims
+    return orc.Grid(nx, ny, nz, st.dx, st.dy, st.dz, st.gamma, emf_mode)
+
+
+def rel_err(gpu, ref):
+    out = []
+    floor = 1e-3 * max(np.abs(ref).max(), 1e-300)
+    for f in range(gpu.shape[0]):
+        scale = max(np.abs(ref[f]).max(), floor)
+        out.append(np.abs(gpu[f] - ref[f]).max() / scale)
+    return np.array(out)
+
+
+def compare(orc, wb, st, dt, nsteps=1, emf_mode=0, integrator="ssprk3", tol=TOL64):
+    g = wb.Grid.from_state(st, precision="fp64", emf_mode=emf_mode, integrator=integrator)
+    g.step(dt, nsteps)
+    U, bx, by, bz = g.get_state_single()
+    g.close()
+    Uo, bxo, byo, bzo = orc.step(ogrid(orc, st, emf_mode), st.U, st.bx, st.by, st.bz, dt,
+                                 nsteps=nsteps, integrator=integrator)
+    eU = rel_err(U, Uo)
+    eb = rel_err(np.stack([bx, by, bz]), np.stack([bxo, byo, bzo]))
+    assert eU.max() <= tol and eb.max() <= tol, (eU, eb)
+    return eU, eb
+
+
+@pytest.mark.parametrize("dims", [(40, 20, 12), (16, 16, 16), (33, 9, 17), (7, 37, 5)])
+def test_fp64_one_step_ragged_tiles(orc, wb, dims):
+    st = I.perturbed(*dims, seed=sum(dims), jump=True)
+    compare(orc, wb, st, 2e-3)
+
+
+def test_fp64_three_steps_emf_modes(orc, wb):
+    st = I.perturbed(24, 20, 16, seed=5, jump=True)
+    compare(orc, wb, st, 2e-3, nsteps=3, emf_mode=0)
+    compare(orc, wb, st, 2e-3, nsteps=3, emf_mode=1)
+
+
+def test_fp64_rk4(orc, wb):
+    st = I.perturbed(20, 16, 12, seed=8, jump=True)
+    compare(orc, wb, st, 2e-3, nsteps=2, integrator="rk4")
+
+
+def test_fp64_turbulence_cfl_steps(orc, wb):
+    st = I.turbulence(32, seed=1808)
+    g = wb.Grid.from_state(st, precision="fp64")
+    g.step_cfl(0.4, 4)
+    U, bx, by, bz = g.get_state_single()
+    t_gpu = g.info()["time"]
+    g.close()
+    Uo, bxo, byo, bzo, dts = orc.step_cfl(ogrid(orc, st), st.U, st.bx, st.by, st.bz, 0.4, nsteps=4)
+    assert t_gpu == pytest.approx(sum(dts), rel=1e-13)
+    eU = rel_err(U, Uo)
+    eb = rel_err(np.stack([bx, by, bz]), np.stack([bxo, byo, bzo]))
+    assert eU.max() <= TOL64 and eb.max() <= TOL64, (eU, eb)
+
+
+def test_alfven_config_fp64(orc, wb):
+    """32^3 Alfven wave, CFL 0.4, 10 steps: parity with the oracle and the
+    exact solution."""
+    st = I.alfven_wave(32, 32, 32, amp=0.1)
+    g = wb.Grid.from_state(st, precision="fp64")
+    g.step_cfl(0.4, 10)
+    U, bx, by, bz = g.get_state_single()
+    t = g.info()["time"]
+    g.close()
+    Uo, bxo, byo, bzo, dts = orc.step_cfl(ogrid(orc, st), st.U, st.bx, st.by, st.bz, 0.4, nsteps=10)
+    assert rel_err(U, Uo).max() <= TOL64
+    assert np.all(bx == 1.0)
+    ex = I.alfven_wave(32, 32, 32, amp=0.1, t=t)
+    assert np.abs(U[5] - ex.U[5]).mean() < 2e-6
+
+
+def test_cfl_dt_and_totals(orc, wb):
+    st = I.turbulence(24, seed=3)
+    g = wb.Grid.from_state(st, precision="fp64")
+    dt = g.cfl_dt(0.4)
+    tot = g.totals()
+    g.close()
+    og = ogrid(orc, st)
+    assert dt == pytest.approx(orc.cfl_dt(og, st.U, st.bx, st.by, st.bz, 0.4), rel=1e-14)
+    ref = orc.totals(og, st.U, st.bx, st.by, st.bz)
+    scale = np.abs(st.U).reshape(8, -1).sum(axis=1) * st.dx * st.dy * st.dz
+    assert np.all(np.abs(tot - ref) <= 1e-14 * np.maximum(scale, 1e-300)), (tot, ref)
+
+
+def test_totals_deterministic_and_conserved(wb):
+    st = I.turbulence(32, seed=4)
+    g = wb.Grid.from_state(st, precision="fp64")
+    t0 = g.totals()
+    assert np.array_equal(t0, g.totals())
+    g.step_cfl(0.4, 3)
+    t1 = g.totals()
+    g.close()
+    scale = np.abs(st.U).reshape(8, -1).sum(axis=1) * st.dx * st.dy * st.dz
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0)
+
+
+def test_batched_patches_fp64(orc, wb):
+    sts = I.patch_batch(5, seed=2, lo=8, hi=20)
+    g = wb.Grid.from_patches(sts, precision="fp64")
+    dt = 0.2 * min(orc.cfl_dt(ogrid(orc, s), s.U, s.bx, s.by, s.bz, 1.0) for s in sts)
+    g.step(dt, 2)
+    U, b = g.get_state()
+    g.close()
+    oU = ob = 0
+    for s in sts:
+        n = s.U[0].size
+        Uo, bxo, byo, bzo = orc.step(ogrid(orc, s), s.U, s.bx, s.by, s.bz, dt, nsteps=2)
+        Ug = U[oU:oU + 8 * n].reshape(Uo.shape)
+        bg = b[ob:ob + 3 * n].reshape((3,) + s.shape)
+        oU += 8 * n
+        ob += 3 * n
+        assert rel_err(Ug, Uo).max() <= TOL64
+        assert rel_err(bg, np.stack([bxo, byo, bzo])).max() <= TOL64
+
+
+def test_thin_grid_and_free_stream(orc, wb):
+    st = I.alfven_wave(16, 1, 1, amp=0.1)
+    compare(orc, wb, st, 2e-3, nsteps=2)
+    st = I.uniform(9, 5, 3)
+    g = wb.Grid.from_state(st, precision="fp64")
+    g.step(1e-2, 3)
+    U, bx, by, bz = g.get_state_single()
+    g.close()
+    assert np.abs(U - st.U).max() <= 4e-16 * np.abs(st.U).max()
+    assert np.array_equal(bx, st.bx) or np.abs(bx - st.bx).max() <= 4e-16
+
+
+def test_fp32_close_to_fp64_oracle(orc, wb):
+    st = I.turbulence(32, seed=11)
+    g = wb.Grid.from_state(st, precision="fp32")
+    dt = orc.cfl_dt(ogrid(orc, st), st.U, st.bx, st.by, st.bz, 0.4)
+    g.step(dt, 3)
+    U, bx, by, bz = g.get_state_single()
+    g.close()
+    Uo, bxo, byo, bzo = orc.step(ogrid(orc, st), st.U, st.bx, st.by, st.bz, dt, nsteps=3)
+    for f in range(8):
+        l1 = np.abs(U[f] - Uo[f]).mean() / max(np.abs(Uo[f]).mean(), 1e-30)
+        assert l1 < 1e-5, (f, l1)
+
+
+def test_nonfinite_state_is_reported(wb):
+    st = I.perturbed(8, 8, 8, seed=1)
+    st.U[0, 3, 3, 3] = np.nan
+    g = wb.Grid.from_state(st, precision="fp64")
+    with pytest.raises(wb.WombatError) as e:
+        g.cfl_dt(0.4)
+    assert e.value.code == wb.WB_ENONFINITE
+    g.close()
