@@ -40,8 +40,8 @@ FP64_FMA_PER_SM_PER_CLK = None   # measured (wb_alu_peak), see the design doc
 # Algorithmic FP operations of one interface of the sweep kernel (one
 # direction, one stage) and of one staged cell, counted from the kernel's
 # formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1); see the design doc.
-SWEEP_FLOPS_PER_INTERFACE = 1350
-SWEEP_FLOPS_PER_STAGED_CELL = 110
+SWEEP_FLOPS_PER_INTERFACE = 2040
+SWEEP_FLOPS_PER_STAGED_CELL = 80
 
 
 def dist_env():

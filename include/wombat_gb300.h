@@ -131,6 +131,15 @@ int wb_get_state(wb_grid *g, double *U_out, double *b_out);
  * asynchronous CFL step. */
 int wb_sync(wb_grid *g);
 
+/* Diagnostic: run the sweep along `axis` (0 x, 1 y, 2 z) on the current
+ * state and copy its numerical fluxes (Sec. 2.1 eq. FWENO, rotated back to
+ * the global frame) to the host.  F_out: host, [7][ncells] FP64 in the
+ * cell layout of wb_get_state (patch-major), entry c holding the flux
+ * through the lower face of cell c along `axis`; components (rho, mx, my,
+ * mz, E, B_t1, B_t2) with (t1, t2) = (y, z), (z, x), (x, y) for axis 0, 1,
+ * 2.  Does not change the state.  Synchronises. */
+int wb_face_fluxes(wb_grid *g, int axis, double *F_out);
+
 /* Kernel classes timed by wb_step_profiled. */
 enum {
     WB_K_SWEEP_X = 0,     /* x-sweep flux kernel (Sec. 2.1 eq. FWENO)         */

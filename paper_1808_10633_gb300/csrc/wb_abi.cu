@@ -280,6 +280,28 @@ int dmalloc(wb_grid* g, P** p, size_t bytes) {
     return WB_OK;
 }
 
+template <class T>
+int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
+    const long long N = g->N;
+    T* flux = static_cast<T*>(g->flux) + (long long)axis * wb::kNFlux * N;
+    wb::SweepArgs<T> a;
+    a.src = static_cast<const T*>(g->un);
+    a.flux = flux;
+    a.er = nullptr;
+    a.tiles = g->d_tiles[axis];
+    a.patches = g->d_patches;
+    a.ncells = N;
+    a.gamma = g->gamma;
+    WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+    // 7 N doubles fit the 11 N staging buffer
+    WB_CK(wb::launch_export_flux<T>(flux, g->d_io, g->d_blocks, g->d_patches, N, g->nblocks,
+                                    g->stream));
+    WB_CK(cudaMemcpyAsync(F_out, g->d_io, sizeof(double) * 7 * N, cudaMemcpyDeviceToHost,
+                          g->stream));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    return WB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -522,6 +544,15 @@ int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
     if (b_out)
         WB_CK(cudaMemcpyAsync(b_out, db, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, g->stream));
     return check_flag(g);
+}
+
+int wb_face_fluxes(wb_grid* g, int axis, double* F_out) {
+    g_err.clear();
+    if (!g || !F_out) return fail(WB_EINVAL, "null argument");
+    if (axis < 0 || axis > 2) return fail(WB_EINVAL, "axis must be 0, 1 or 2");
+    WB_CK(cudaSetDevice(g->device));
+    return g->precision == WB_FP64 ? face_fluxes_impl<double>(g, axis, F_out)
+                                   : face_fluxes_impl<float>(g, axis, F_out);
 }
 
 int wb_sync(wb_grid* g) {

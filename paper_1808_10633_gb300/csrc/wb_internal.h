@@ -85,6 +85,10 @@ cudaError_t launch_import(const double* U, const double* b, T* state,
                           const CellBlock* blocks, const PatchDev* patches,
                           long long ncells, int nblocks, cudaStream_t s);
 template <class T>
+cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* blocks,
+                               const PatchDev* patches, long long ncells, int nblocks,
+                               cudaStream_t s);
+template <class T>
 cudaError_t launch_export(const T* state, double* U, double* b,
                           const CellBlock* blocks, const PatchDev* patches,
                           long long ncells, int nblocks, cudaStream_t s);

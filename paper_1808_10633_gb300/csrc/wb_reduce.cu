@@ -209,7 +209,32 @@ export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restric
     }
 }
 
+// Face fluxes of one axis to the ABI's patch-major FP64 layout [7][cells].
+template <class T>
+__global__ void __launch_bounds__(kCellBlock)
+export_flux_kernel(const T* __restrict__ F, double* __restrict__ out,
+                   const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
+                   long long N) {
+    const CellBlock cb = blocks[blockIdx.x];
+    const PatchDev P = patches[cb.x];
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    const int local = cb.y + threadIdx.x;
+    if (local >= np) return;
+    const long long c = P.off + local;
+    double* o = out + 7 * P.off + local;
+#pragma unroll
+    for (int q = 0; q < 7; q++) o[q * np] = double(F[q * N + c]);
+}
+
 }  // namespace
+
+template <class T>
+cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* blocks,
+                               const PatchDev* patches, long long ncells, int nblocks,
+                               cudaStream_t s) {
+    export_flux_kernel<T><<<nblocks, kCellBlock, 0, s>>>(flux, out, blocks, patches, ncells);
+    return cudaGetLastError();
+}
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
@@ -262,7 +287,9 @@ cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock*
     template cudaError_t launch_import<T>(const double*, const double*, T*, const CellBlock*, \
                                           const PatchDev*, long long, int, cudaStream_t);     \
     template cudaError_t launch_export<T>(const T*, double*, double*, const CellBlock*,       \
-                                          const PatchDev*, long long, int, cudaStream_t);
+                                          const PatchDev*, long long, int, cudaStream_t);     \
+    template cudaError_t launch_export_flux<T>(const T*, double*, const CellBlock*,           \
+                                               const PatchDev*, long long, int, cudaStream_t);
 WB_INST(float)
 WB_INST(double)
 #undef WB_INST

@@ -25,7 +25,7 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 # every entry point declared in include/wombat_gb300.h
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
-           "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak")
+           "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes")
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals")
 
 
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
     L.wb_destroy.argtypes = [vp]
     L.wb_step_profiled.argtypes = [vp, d, i, i, dp, ctypes.POINTER(ctypes.c_int), dp]
     L.wb_alu_peak.argtypes = [i, dp]
+    L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_last_error.restype = ctypes.c_char_p
     L.wb_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -190,6 +191,12 @@ class Grid:
         U, b = self.get_state()
         b = b.reshape(3, nz, ny, nx)
         return U.reshape(8, nz, ny, nx), b[0], b[1], b[2]
+
+    def face_fluxes(self, axis: int) -> np.ndarray:
+        """Numerical fluxes of one sweep on the current state, (7, ncells)."""
+        out = np.empty(7 * self.ncells)
+        _check(self._lib.wb_face_fluxes(self._h, int(axis), out.ctypes.data))
+        return out.reshape(7, self.ncells)
 
     def sync(self):
         _check(self._lib.wb_sync(self._h))
