@@ -176,6 +176,42 @@ int wb_destroy(wb_grid *g);
 /* Message of the last failing call on this thread ("" if none). */
 const char *wb_last_error(void);
 
+/* Conserved totals for callers that cannot allocate device memory.
+ *
+ * Some callers cannot call cudaMalloc: code that runs under another
+ * component's device memory pool (a framework that owns the device's memory
+ * and forbids allocations it does not make), or a time-critical loop where
+ * the implicit device synchronisation of cudaMalloc/cudaFree is not
+ * acceptable.  This entry point computes the same deterministic FP64 sums as
+ * wb_conserved_totals, but on a state held in the caller's device memory and
+ * without allocating anything: its per-block partial sums live in a
+ * file-scope device array of WB_NOALLOC_PARTIALS x 8 doubles (64 KiB), which
+ * every GPU that loads the library holds until the process exits.  The paper
+ * has no counterpart; it is an interface convenience.
+ *
+ * state: device, 8 arrays of ncells values, array f at state + f*ncells, in
+ *   the order rho, mx, my, mz, E, bx, by, bz (bx/by/bz on the lower faces of
+ *   periodic patches, so that their sums equal the sums of the cell means);
+ *   element type double for precision WB_FP64, float for WB_FP32.
+ * ncells: 1 .. WB_NOALLOC_MAX_CELLS; larger values return WB_EINVAL with a
+ *   message.
+ * dV: cell volume the sums are multiplied by.
+ * out: device, 8 doubles: totals of (rho, mx, my, mz, Bx, By, Bz, E) * dV.
+ * cuda_stream: cudaStream_t to order the work on (NULL: the default stream).
+ * Asynchronous: out is valid once the stream has been synchronised.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one scratch array, so
+ * calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  Each call rewrites every partial
+ * slot it reads, so nothing needs clearing between calls.
+ * Errors: WB_EINVAL (null pointer, unknown precision, ncells out of range),
+ * WB_ECUDA. */
+#define WB_NOALLOC_PARTIALS 1024
+#define WB_NOALLOC_MAX_CELLS (1LL << 34)
+int wb_conserved_totals_noalloc(const void *state, int precision, long long ncells,
+                                double dV, double *out, void *cuda_stream);
+
 /* Library version string. */
 const char *wb_version(void);
 

@@ -304,6 +304,11 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
 
 }  // namespace
 
+int wb::set_last_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+
 extern "C" {
 
 const char* wb_last_error(void) { return g_err.c_str(); }

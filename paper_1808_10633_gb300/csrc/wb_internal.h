@@ -57,6 +57,9 @@ struct UpdateArgs {
     int emf_mode;
 };
 
+// Sets the calling thread's wb_last_error() message and returns `code`.
+int set_last_error(int code, const char* msg);
+
 // ---- launchers (one per translation unit) ---------------------------------
 template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s);

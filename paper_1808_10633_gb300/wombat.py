@@ -25,7 +25,8 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 # every entry point declared in include/wombat_gb300.h
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
-           "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes")
+           "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
+           "wb_conserved_totals_noalloc")
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals")
 
 
@@ -78,6 +79,7 @@ def load() -> ctypes.CDLL:
     L.wb_step_profiled.argtypes = [vp, d, i, i, dp, ctypes.POINTER(ctypes.c_int), dp]
     L.wb_alu_peak.argtypes = [i, dp]
     L.wb_face_fluxes.argtypes = [vp, i, vp]
+    L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
     L.wb_last_error.restype = ctypes.c_char_p
     L.wb_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -222,6 +224,16 @@ class Grid:
 
     def __exit__(self, *a):
         self.close()
+
+
+def conserved_totals_noalloc(state_ptr: int, precision, ncells: int, dV: float, out_ptr: int,
+                             stream=None):
+    """Totals of a caller-owned device state (device pointers), no allocation.
+    See wb_conserved_totals_noalloc in include/wombat_gb300.h."""
+    p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    _check(load().wb_conserved_totals_noalloc(ctypes.c_void_p(state_ptr), int(p), int(ncells),
+                                              float(dV), ctypes.c_void_p(out_ptr),
+                                              ctypes.c_void_p(int(stream)) if stream else None))
 
 
 def version() -> str:
