@@ -133,8 +133,8 @@ def sweep_units(n):
     from paper_1808_10633_gb300 import wombat  # noqa: F401  (library must load)
     iface = n ** 3
     # x: tiles of 32 interfaces x 8 pencils stage 37 cells per pencil;
-    # y, z: tiles of 8 x 32 stage 13 cells per pencil.
-    staged = {"sweep_x": n ** 3 * 37 / 32, "sweep_y": n ** 3 * 13 / 8, "sweep_z": n ** 3 * 13 / 8}
+    # y, z: tiles of 16 x 16 stage 21 cells per pencil.
+    staged = {"sweep_x": n ** 3 * 37 / 32, "sweep_y": n ** 3 * 21 / 16, "sweep_z": n ** 3 * 21 / 16}
     return iface, staged
 
 
@@ -150,7 +150,7 @@ def run_native(args, rank, world, local):
     clocks = Clocks(args.phys_gpu, os.path.join(args.out_dir, f"clocks_rank{rank}.csv") if args.out_dir else None)
 
     peak32 = wombat.alu_peak_tflops("fp32")
-    peak64 = wombat.alu_peak_tflops("fp64")
+    peak64 = wombat.alu_peak_tflops("fp64") if not args.fp32_only else None
 
     # ---- FP32 bulk (headline) -------------------------------------------
     g32 = wombat.Grid.from_state(st, precision="fp32")
@@ -165,15 +165,18 @@ def run_native(args, rank, world, local):
         torch.cuda.synchronize()
         barrier(world)
         # FP64 path inside the same clock window
-        g64 = wombat.Grid.from_state(st, precision="fp64")
-        g64.step_cfl(args.cfl, 1)
-        g64.sync()
-        k64 = max(2, args.steps // 4)
-        tot64, kms64, kcnt64 = g64.step_profiled(args.cfl, k64, with_totals=True)
+        g64 = None
+        if not args.fp32_only:
+            g64 = wombat.Grid.from_state(st, precision="fp64")
+            g64.step_cfl(args.cfl, 1)
+            g64.sync()
+            k64 = max(2, args.steps // 4)
+            tot64, kms64, kcnt64 = g64.step_profiled(args.cfl, k64, with_totals=True)
     secs = max_over_ranks(tot_ms / 1e3, world)
     value = world * zones * args.steps / secs
-    secs64 = max_over_ranks(tot64 / 1e3, world)
-    value64 = world * zones * k64 / secs64
+    if g64 is not None:
+        secs64 = max_over_ranks(tot64 / 1e3, world)
+        value64 = world * zones * k64 / secs64
     clk = clocks.summary()
 
     # graph-replay timing of the same step (no per-kernel events)
@@ -196,12 +199,11 @@ def run_native(args, rank, world, local):
                 "peak_source": "measured FMA throughput (wb_alu_peak) on this GPU"}
 
     rf32 = roofline(kms, kcnt, peak32, "float")
-    rf64 = roofline(kms64, kcnt64, peak64, "double")
-    g64_state = None
+    rf64 = roofline(kms64, kcnt64, peak64, "double") if g64 is not None else None
 
     # ---- FP32 vs FP64 L1 error after l1_steps fixed-dt steps (rank 0) ----
     l1 = None
-    if rank == 0 and args.l1_steps > 0:
+    if rank == 0 and args.l1_steps > 0 and g64 is not None:
         g64.set_state(st.U, np.stack([st.bx, st.by, st.bz]))
         g32.set_state(st.U, np.stack([st.bx, st.by, st.bz]))
         dt = g64.cfl_dt(args.cfl)
@@ -217,8 +219,8 @@ def run_native(args, rank, world, local):
             d = np.abs(U32[f] - U64[f])
             l1[nm] = {"l1_rel": float(d.mean() / max(np.abs(U64[f]).mean(), 1e-300)),
                       "linf_rel": float(d.max() / max(np.abs(U64[f]).max(), 1e-300))}
-        g64_state = True
-    g64.close()
+    if g64 is not None:
+        g64.close()
 
     # ---- end to end through the ABI with pinned host buffers --------------
     e2e = None
@@ -262,7 +264,8 @@ def run_native(args, rank, world, local):
         "graph_replay_ms_per_step": graph_ms,
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "roofline": rf32,
-        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": secs64 * 1e3 / k64, "steps": k64,
+        "fp64": None if g64 is None else
+                {"value": value64, "unit": UNIT, "ms_per_step": secs64 * 1e3 / k64, "steps": k64,
                  "kernel_ms_per_step": {k: v / k64 for k, v in kms64.items()}, "roofline": rf64},
         "fp32_vs_fp64_after_steps": args.l1_steps if l1 else 0,
         "fp32_error_vs_fp64": l1,
@@ -338,10 +341,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp32-only", action="store_true",
+                    help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.fp32_only:
+        args.no_e2e = args.no_cpu = True
+        args.l1_steps = 0
     rank, world, local = dist_env()
     # one GPU per rank: restrict this process to its GPU before CUDA starts,
     # so that torch and the library see the same device 0

@@ -145,11 +145,12 @@ enum {
     WB_K_SWEEP_X = 0,     /* x-sweep flux kernel (Sec. 2.1 eq. FWENO)         */
     WB_K_SWEEP_Y = 1,
     WB_K_SWEEP_Z = 2,
-    WB_K_UPDATE = 3,      /* flux difference + constrained transport + RK     */
+    WB_K_UPDATE = 3,      /* flux difference + face -curl E + RK combine      */
     WB_K_CFL = 4,         /* CFL max reduction                                */
     WB_K_DT = 5,          /* dt from the reduced speed                        */
     WB_K_TOTALS = 6,      /* conserved totals (two kernels)                   */
-    WB_NKERNEL = 7
+    WB_K_EMF = 7,         /* edge EMFs of constrained transport               */
+    WB_NKERNEL = 8
 };
 
 /* Measurement helper: advance nsteps CFL steps exactly as wb_step_cfl does,
@@ -211,6 +212,38 @@ const char *wb_last_error(void);
 #define WB_NOALLOC_MAX_CELLS (1LL << 34)
 int wb_conserved_totals_noalloc(const void *state, int precision, long long ncells,
                                 double dV, double *out, void *cuda_stream);
+
+/* ---- learned WENO weights ------------------------------------------------
+ * One network per characteristic field s = 0..6 (waves u-cf, u-ca, u-cs, u,
+ * u+cs, u+ca, u+cf): 6 -> 32 -> 32 -> 3 with GELU (tanh form) and softmax,
+ * predicting the weights (w0, w1, w2) that phi_N (Sec. 2.1) uses in place of
+ * the Jiang-Shu weights.  Parameters: WB_MLP_NFIELD blocks of WB_MLP_NPARAM
+ * floats, each W1 (32x6 row-major), b1, W2 (32x32), b2, W3 (3x32), b3.
+ * Training records: WB_MLP_RECORD floats each: field, x[6] (normalised
+ * stencil), q[3] (normalised third-order candidate fluxes), T (normalised
+ * target reconstruction), flag (non-zero: excluded from training).  The
+ * paper has no learned component; this follows the readings recorded with
+ * the design notes. */
+#define WB_MLP_NFIELD 7
+#define WB_MLP_NPARAM 1379
+#define WB_MLP_RECORD 12
+
+/* Mean loss per field (loss_out[7]) and its gradient (grad_out[7*1379])
+ * over all unflagged records (host arrays), computed on the GPU by the
+ * library's forward and backward kernels; loss per record
+ * (sum_k w_k q_k - T)^2 + lam * sum_k d_k log(d_k / w_k), d = (0.1,0.6,0.3).
+ * Deterministic.  Synchronises. */
+int wb_mlp_loss_grad(const float *records, long long n, const float *params,
+                     double lam, double *loss_out, float *grad_out);
+
+/* Adam training of all seven networks: `steps` steps, `batch` records per
+ * field per step drawn by a counter-based generator from `seed`; params
+ * (host, in/out) starts from the given values; loss_history (host,
+ * steps*7, may be NULL) receives each step's minibatch loss per field.
+ * Synchronises. */
+int wb_mlp_train(const float *records, long long n, float *params, int steps,
+                 int batch, double lr, double lam, unsigned long long seed,
+                 float *loss_history);
 
 /* Library version string. */
 const char *wb_version(void);

@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwombat_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-file extra flags: the FP32 sweep uses fast single-precision division
+# and square root (FP64 code in that file is unaffected)
+EXTRA = {"wb_sweep_f32.cu": ["-use_fast_math"]}
 
 
 def nvcc() -> str:
@@ -31,6 +34,8 @@ def nvcc() -> str:
 def flags(verbose: bool = False):
     f = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+    # tuning knobs of the kernels (e.g. -DWB_SWEEP_TA_YZ=8), for experiments
+    f += os.environ.get("WB_NVCC_FLAGS", "").split()
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -61,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *flags(verbose), "-c", src, "-o", obj]
+        cmd = [cc, *flags(verbose), *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -7,8 +7,9 @@
 //   acc  8 arrays  RK4 accumulator (RK4 only)
 //   flux 21 arrays 7 face-flux components per axis
 //   er   3 arrays  cell -v x B for the edge EMFs (emf_mode 0 only)
-// One step = [CFL reduction + dt] + per stage: x, y, z sweeps and the
-// update kernel.  A step is captured once as a CUDA graph and replayed.
+//   emf  3 arrays  edge EMFs of the current stage
+// One step = [CFL reduction + dt] + per stage: x, y, z sweeps, the edge-EMF
+// kernel and the update kernel.  A step is captured once as a CUDA graph and replayed.
 #include "../../include/wombat_gb300.h"
 #include "wb_internal.h"
 
@@ -83,6 +84,7 @@ struct wb_grid {
     void* acc = nullptr;
     void* flux = nullptr;
     void* er = nullptr;
+    void* emf = nullptr;
     wb::PatchDev* d_patches = nullptr;
     std::vector<wb::PatchDev> h_patches;
     wb::Tile* d_tiles[3] = {nullptr, nullptr, nullptr};
@@ -146,8 +148,12 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
         u.stage = st;
         u.integrator = g->integrator;
         u.emf_mode = g->emf_mode;
+        u.emf = static_cast<T*>(g->emf);
         int rc = prof_begin(pf, g->stream);
         if (rc != WB_OK) return rc;
+        WB_CK(wb::launch_emf<T>(u, g->nblocks, g->stream));
+        if ((rc = prof_end(pf, g->stream, WB_K_EMF)) != WB_OK) return rc;
+        if ((rc = prof_begin(pf, g->stream)) != WB_OK) return rc;
         WB_CK(wb::launch_update<T>(u, g->nblocks, g->stream));
         if ((rc = prof_end(pf, g->stream, WB_K_UPDATE)) != WB_OK) return rc;
     }
@@ -263,7 +269,7 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->d_patches, g->d_tiles[0],
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_patches, g->d_tiles[0],
                     g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_scalars, g->d_smax,
                     g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
@@ -403,6 +409,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (g->integrator == WB_RK4 && (rc = dmalloc(g, &g->acc, T * 8 * N))) return bail(rc);
     if ((rc = dmalloc(g, &g->flux, T * 3 * wb::kNFlux * N))) return bail(rc);
     if (g->emf_mode == 0 && (rc = dmalloc(g, &g->er, T * 3 * N))) return bail(rc);
+    if ((rc = dmalloc(g, &g->emf, T * 3 * N))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_patches, sizeof(wb::PatchDev) * g->npatch))) return bail(rc);
     for (int a = 0; a < 3; a++)
         if ((rc = dmalloc(g, &g->d_tiles[a], sizeof(wb::Tile) * tiles[a].size()))) return bail(rc);
@@ -465,7 +472,7 @@ int wb_step_profiled(wb_grid* g, double cfl, int nsteps, int with_totals, double
     if (!g || !kernel_ms || !launches || !total_ms) return fail(WB_EINVAL, "null argument");
     if (!(cfl > 0) || nsteps < 1) return fail(WB_EINVAL, "need cfl > 0 and nsteps >= 1");
     WB_CK(cudaSetDevice(g->device));
-    const int per_step = 2 + (g->integrator == WB_RK4 ? 4 : 3) * 4 + (with_totals ? 1 : 0);
+    const int per_step = 2 + (g->integrator == WB_RK4 ? 4 : 3) * 5 + (with_totals ? 1 : 0);
     Prof pf;
     pf.ev.resize((size_t)2 * per_step * nsteps, nullptr);
     int rc = WB_OK;

@@ -47,6 +47,7 @@ struct UpdateArgs {
     T* acc;                        // RK4 accumulator (may be null)
     const T* __restrict__ flux;    // 3 axes x kNFlux arrays
     const T* __restrict__ er;      // 3 arrays (emf_mode 0) or nullptr
+    T* emf;                        // 3 arrays of edge EMFs (E_x, E_y, E_z)
     const CellBlock* __restrict__ blocks;
     const PatchDev* __restrict__ patches;
     const double* __restrict__ dt; // device scalar
@@ -68,7 +69,14 @@ cudaError_t prepare_sweep_kernels();
 void sweep_tile_shape(int axis, int* ta, int* tp);
 
 template <class T>
+cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
+template <class T>
 cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
+
+template <class T>
+cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, int axis,
+                           const long long* cells, long long n, const double* hU, const double* hF,
+                           double gamma, double kappa, double pjump, float* out, cudaStream_t s);
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,

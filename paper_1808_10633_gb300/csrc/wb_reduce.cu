@@ -11,7 +11,10 @@ namespace {
 __device__ __forceinline__ int inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 
 // dt rule: s = sum_d (|v_d| + c_f,d) / dx_d per cell, maximised over cells;
-// the fast speed along d uses B_d as the normal field.  All in FP64.
+// the fast speed along d uses B_d as the normal field.  The per-cell speed is
+// taken in the state's precision (FP32 in FP32 mode: FP64 division and square
+// root run at a small fraction of the FP32 rate on this GPU); the maximum is
+// reduced in FP64, which is exact.
 template <class T>
 __global__ void __launch_bounds__(kCellBlock)
 cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
@@ -31,30 +34,33 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
         const long long cx = c + (inc(i, P.nx) - i);
         const long long cy = c + (long long)(inc(j, P.ny) - j) * P.nx;
         const long long cz = c + (long long)(inc(k, P.nz) - k) * nxy;
-        const double rho = q[c];
-        const double v[3] = {double(q[N + c]) / rho, double(q[2 * N + c]) / rho,
-                             double(q[3 * N + c]) / rho};
-        const double B[3] = {0.5 * (double(q[5 * N + c]) + double(q[5 * N + cx])),
-                             0.5 * (double(q[6 * N + c]) + double(q[6 * N + cy])),
-                             0.5 * (double(q[7 * N + c]) + double(q[7 * N + cz]))};
-        const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-        const double kin = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        const double p = (gamma - 1.0) * (double(q[4 * N + c]) - kin - 0.5 * bb);
-        const double a2 = gamma * p / rho;
-        const double b2 = bb / rho;
-        const double sum = a2 + b2;
-        const double id[3] = {idx, idy, idz};
+        const T g = T(gamma);
+        const T rho = q[c];
+        const T rinv = T(1) / rho;
+        const T v[3] = {q[N + c] * rinv, q[2 * N + c] * rinv, q[3 * N + c] * rinv};
+        const T B[3] = {T(0.5) * (q[5 * N + c] + q[5 * N + cx]),
+                        T(0.5) * (q[6 * N + c] + q[6 * N + cy]),
+                        T(0.5) * (q[7 * N + c] + q[7 * N + cz])};
+        const T bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const T kin = T(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const T p = (g - T(1)) * (q[4 * N + c] - kin - T(0.5) * bb);
+        const T a2 = g * p * rinv;
+        const T b2 = bb * rinv;
+        const T sum = a2 + b2;
+        const T id[3] = {T(idx), T(idy), T(idz)};
+        T sp = T(0);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double ca2 = B[d] * B[d] / rho;
-            double disc = sum * sum - 4.0 * a2 * ca2;
-            disc = disc > 0.0 ? disc : 0.0;
-            const double cf = sqrt(0.5 * (sum + sqrt(disc)));
-            s += (fabs(v[d]) + cf) * id[d];
+            const T ca2 = B[d] * B[d] * rinv;
+            T disc = sum * sum - T(4) * a2 * ca2;
+            disc = disc > T(0) ? disc : T(0);
+            const T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
+            sp += (fabs(v[d]) + cf) * id[d];
         }
+        s = double(sp);
         unsigned int bad = 0;
         if (!(s <= DBL_MAX)) bad |= 1u;              // NaN or Inf
-        if (!(rho > 0.0) || !(p > 0.0)) bad |= 2u;
+        if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
         if (bad) {
             atomicOr(flag, bad);
             s = 0.0;

@@ -1,5 +1,7 @@
-// wb_sweep.cu -- characteristic WENO5 flux sweeps (Donnert et al. 2018,
-// Sec. 2.1 eq. FWENO; Sec. 2.2 dimension-by-dimension sweeps).
+// wb_sweep.cuh -- characteristic WENO5 flux sweeps (Donnert et al. 2018,
+// Sec. 2.1 eq. FWENO; Sec. 2.2 dimension-by-dimension sweeps).  Included by
+// wb_sweep_f32.cu (compiled with fast single-precision division and square
+// root) and wb_sweep_f64.cu, which instantiate it for float and double.
 //
 // One thread computes the numerical flux through one interface.  A block
 // owns a 2-D slab of interfaces: TA along the sweep axis times TP pencils.
@@ -25,7 +27,15 @@
 //      the fourth-order central flux (-F_{i-1} + 7F_i + 7F_{i+1} - F_{i+2})/12.
 // The flux is written in global component order (rho, mx, my, mz, E,
 // B_t1, B_t2) to the face array of the lower face of cell i+1.
+#pragma once
+#include "../../include/wombat_gb300.h"
 #include "wb_internal.h"
+
+// Characteristic fields are projected two groups at a time (fast+slow,
+// then Alfven+entropy) by default; 4 processes one field pair at a time.
+#ifndef WB_SWEEP_GROUPS
+#define WB_SWEEP_GROUPS 2
+#endif
 
 namespace wb {
 namespace {
@@ -108,12 +118,23 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
 // need, with 1/rho and (gamma-1) folded into the left coefficients.
 template <class T>
 struct Eig {
-    T rho, u, v1, v2, b1, b2, hv2, gm1;
-    T be1, be2, S;
-    T alf, als, cf, cs, a, sr, a2;
+    T rho, u, v1, v2, b1, b2, hv2;
+    T be1, be2;
+    T cf, cs, ca;
     T Af, Bf, Cf, Df, As, Bs, Cs, Ds, Aa, Ba, Ee;
-    T lam[7];
 };
+
+// Coefficients only the back-projection needs; parked in shared memory (one
+// slot per thread) while the WENO step runs, to keep registers for it.
+enum : int { BP_ALF = 0, BP_ALS, BP_AFCF, BP_ASCS, BP_ASR, BP_SSR, BP_RA2, BP_IGM1, kNBack = 8 };
+
+// |lambda_s| of the interface state, s = 0..6 (u-cf, u-ca, u-cs, u, u+cs,
+// u+ca, u+cf)
+template <class T>
+__device__ __forceinline__ T lam_avg(const Eig<T>& e, int s) {
+    const T c = (s == 0 || s == 6) ? e.cf : (s == 1 || s == 5) ? e.ca : (s == 2 || s == 4) ? e.cs : T(0);
+    return tabs(s < 3 ? e.u - c : e.u + c);
+}
 
 // beta and (alpha_f, alpha_s) with the degeneracy rules; FP64 throughout.
 __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b1, double b2,
@@ -154,7 +175,7 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
 
 template <class T>
 __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, T p, T gamma,
-                                      Eig<T>& e) {
+                                      Eig<T>& e, T* __restrict__ bp, int bstride) {
     const T rinv = T(1) / rho;
     const T a2 = gamma * p * rinv;
     const T ca2 = bn * bn * rinv;
@@ -203,9 +224,16 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
     const T hgp = T(0.5) * gm1 / (gamma * p); // (gamma-1) / (2 rho a^2)
     e.rho = rho; e.u = u; e.v1 = v1; e.v2 = v2; e.b1 = b1; e.b2 = b2;
     e.hv2 = T(0.5) * (u * u + v1 * v1 + v2 * v2);
-    e.gm1 = gm1;
-    e.be1 = be1; e.be2 = be2; e.S = S;
-    e.alf = alf; e.als = als; e.cf = cf; e.cs = cs; e.a = a; e.sr = sr; e.a2 = a2;
+    e.be1 = be1; e.be2 = be2;
+    e.cf = cf; e.cs = cs; e.ca = ca;
+    bp[BP_ALF * bstride] = alf;
+    bp[BP_ALS * bstride] = als;
+    bp[BP_AFCF * bstride] = alf * cf;
+    bp[BP_ASCS * bstride] = als * cs;
+    bp[BP_ASR * bstride] = a * sr;
+    bp[BP_SSR * bstride] = S * sr;
+    bp[BP_RA2 * bstride] = rho * a2;
+    bp[BP_IGM1 * bstride] = T(1) / gm1;
     e.Af = alf * cf * hXr;
     e.Bf = -als * cs * S * hXr;
     e.Cf = als * hia;
@@ -217,32 +245,47 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
     e.Aa = T(0.5) * rinv;
     e.Ba = T(0.5) * S * isr;
     e.Ee = gm1 / a2;
-    e.lam[0] = tabs(u - cf); e.lam[1] = tabs(u - ca); e.lam[2] = tabs(u - cs);
-    e.lam[3] = tabs(u);
-    e.lam[4] = tabs(u + cs); e.lam[5] = tabs(u + ca); e.lam[6] = tabs(u + cf);
 }
 
-// ---- staging --------------------------------------------------------------
+// ---- staging ---------------------------------------------------------------
 // Per cell: cell B from the faces, rotation into the (n, t1, t2) frame,
 // primitives, the physical flux along n, the seven |lambda| and, in the x
-// sweep, the cell value of -v x B for the constrained-transport EMFs.
-template <class T, int AXIS>
-__device__ __forceinline__ void stage_cell(const SweepArgs<T>& A, const PatchDev& P,
-                                           int i, int j, int k, T* __restrict__ sm,
-                                           int nc, int idx, bool write_er) {
+// sweep, the cell value of -v x B for the constrained-transport EMFs.  The
+// loads of all cells a thread stages are issued first (load_cell), the
+// derived quantities computed afterwards (derive_cell), so one global-load
+// latency covers a thread's whole share of the tile.
+template <class T>
+struct RawCell {
+    T rho, mx, my, mz, E, bx0, bx1, by0, by1, bz0, bz1;
+};
+
+template <class T>
+__device__ __forceinline__ void load_cell(const SweepArgs<T>& A, const PatchDev& P, int i, int j,
+                                          int k, RawCell<T>& r, long long& c) {
     const long long N = A.ncells;
     const T* __restrict__ q = A.src;
-    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
+    c = P.off + ((long long)k * P.ny + j) * P.nx + i;
     const int ip = (i + 1 == P.nx) ? 0 : i + 1;
     const int jp = (j + 1 == P.ny) ? 0 : j + 1;
     const int kp = (k + 1 == P.nz) ? 0 : k + 1;
     const long long cxp = c + (ip - i);
     const long long cyp = c + (long long)(jp - j) * P.nx;
     const long long czp = c + (long long)(kp - k) * P.nx * P.ny;
-    const T rho = q[c], mx = q[N + c], my = q[2 * N + c], mz = q[3 * N + c], E = q[4 * N + c];
-    const T Bx = T(0.5) * (q[5 * N + c] + q[5 * N + cxp]);
-    const T By = T(0.5) * (q[6 * N + c] + q[6 * N + cyp]);
-    const T Bz = T(0.5) * (q[7 * N + c] + q[7 * N + czp]);
+    r.rho = q[c]; r.mx = q[N + c]; r.my = q[2 * N + c]; r.mz = q[3 * N + c]; r.E = q[4 * N + c];
+    r.bx0 = q[5 * N + c]; r.bx1 = q[5 * N + cxp];
+    r.by0 = q[6 * N + c]; r.by1 = q[6 * N + cyp];
+    r.bz0 = q[7 * N + c]; r.bz1 = q[7 * N + czp];
+}
+
+template <class T, int AXIS>
+__device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell<T>& r, long long c,
+                                            T* __restrict__ sm, int nc, int idx, bool write_er) {
+    const long long N = A.ncells;
+    const T rho = r.rho, E = r.E;
+    const T Bx = T(0.5) * (r.bx0 + r.bx1);
+    const T By = T(0.5) * (r.by0 + r.by1);
+    const T Bz = T(0.5) * (r.bz0 + r.bz1);
+    const T mx = r.mx, my = r.my, mz = r.mz;
     T mn, m1, m2, bn, b1, b2;
     if (AXIS == 0) { mn = mx; m1 = my; m2 = mz; bn = Bx; b1 = By; b2 = Bz; }
     else if (AXIS == 1) { mn = my; m1 = mz; m2 = mx; bn = By; b1 = Bz; b2 = Bx; }
@@ -338,6 +381,36 @@ __device__ __forceinline__ void project_ae(const Eig<T>& e, const T (&x)[7], T (
     o[2] = t1 - t2;
 }
 
+// single field pair projections (fields processed two at a time keep the
+// projected stencil small): G = 0 fast-/fast+ (s = 0, 6), 1 slow-/slow+
+// (s = 2, 4), 2 Alfven-/Alfven+ (s = 1, 5), 3 entropy (s = 3).
+template <int G, class T>
+__device__ __forceinline__ void project_pair(const Eig<T>& e, const T (&x)[7], T (&o)[2]) {
+    const T dv1 = x[2] - e.v1 * x[0];
+    const T dv2 = x[3] - e.v2 * x[0];
+    if constexpr (G == 2) {
+        const T t1 = e.Aa * (e.be1 * dv2 - e.be2 * dv1);
+        const T t2 = e.Ba * (e.be1 * x[5] - e.be2 * x[4]);
+        o[0] = t1 + t2;
+        o[1] = t1 - t2;
+    } else {
+        const T P = x[6] + e.hv2 * x[0] - e.u * x[1] - e.v1 * x[2] - e.v2 * x[3]
+                  - e.b1 * x[4] - e.b2 * x[5];
+        if constexpr (G == 3) {
+            o[0] = x[0] - e.Ee * P;
+            o[1] = o[0];
+        } else {
+            const T du = x[1] - e.u * x[0];
+            const T vpar = e.be1 * dv1 + e.be2 * dv2;
+            const T bpar = e.be1 * x[4] + e.be2 * x[5];
+            const T t1 = G == 0 ? e.Af * du + e.Bf * vpar : e.As * du + e.Bs * vpar;
+            const T t2 = G == 0 ? e.Cf * bpar + e.Df * P : e.Cs * bpar + e.Ds * P;
+            o[0] = t2 - t1;
+            o[1] = t2 + t1;
+        }
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const int (&id)[6],
                                       int s, T lam_avg) {
@@ -349,7 +422,8 @@ __device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const in
 
 template <class T>
 __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc, const int (&id)[6],
-                                               T gamma, T (&out)[7]) {
+                                               T gamma, T* __restrict__ bp, int bstride,
+                                               T (&out)[7]) {
     // 1-2. interface state and eigen-structure
     Eig<T> e;
     {
@@ -362,20 +436,40 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
                  h * (sm[SP_BN * nc + l] + sm[SP_BN * nc + r]),
                  h * (sm[(SU + 4) * nc + l] + sm[(SU + 4) * nc + r]),
                  h * (sm[(SU + 5) * nc + l] + sm[(SU + 5) * nc + r]),
-                 h * (sm[SP_P * nc + l] + sm[SP_P * nc + r]), gamma, e);
+                 h * (sm[SP_P * nc + l] + sm[SP_P * nc + r]), gamma, e, bp, bstride);
     }
     T corr[7];
-    // central flux (-F_{i-1} + 7F_i + 7F_{i+1} - F_{i+2}) / 12
+#if WB_SWEEP_GROUPS == 4
+    // 3-5. one field pair at a time
     {
-        T f1[7], f2[7], f3[7], f4[7];
-        load7(sm, nc, SF, id[1], f1);
-        load7(sm, nc, SF, id[2], f2);
-        load7(sm, nc, SF, id[3], f3);
-        load7(sm, nc, SF, id[4], f4);
+        constexpr int NP = 4;
+        constexpr int s0[NP] = {0, 2, 1, 3};
+        constexpr int s1[NP] = {6, 4, 5, 3};
 #pragma unroll
-        for (int f = 0; f < 7; f++)
-            out[f] = (T(7) * (f2[f] + f3[f]) - (f1[f] + f4[f])) * T(1.0 / 12.0);
+        for (int G = 0; G < NP; G++) {
+            T w[2][6], g[2][6];
+#pragma unroll
+            for (int m = 0; m < 6; m++) {
+                T x[7], o[2];
+                load7(sm, nc, SU, id[m], x);
+                if (G == 0) project_pair<0>(e, x, o);
+                else if (G == 1) project_pair<1>(e, x, o);
+                else if (G == 2) project_pair<2>(e, x, o);
+                else project_pair<3>(e, x, o);
+                w[0][m] = o[0]; w[1][m] = o[1];
+                load7(sm, nc, SF, id[m], x);
+                if (G == 0) project_pair<0>(e, x, o);
+                else if (G == 1) project_pair<1>(e, x, o);
+                else if (G == 2) project_pair<2>(e, x, o);
+                else project_pair<3>(e, x, o);
+                g[0][m] = o[0]; g[1][m] = o[1];
+            }
+            corr[s0[G]] = weno_corr<T>(w[0], g[0], lf_speed(sm, nc, id, s0[G], lam_avg(e, s0[G])));
+            if (G != 3)
+                corr[s1[G]] = weno_corr<T>(w[1], g[1], lf_speed(sm, nc, id, s1[G], lam_avg(e, s1[G])));
+        }
     }
+#else
     // 3-5. fast and slow fields
     {
         T w[4][6], g[4][6];
@@ -394,7 +488,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #pragma unroll
         for (int f = 0; f < 4; f++) {
             const int s = 2 * f;
-            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, e.lam[s]));
+            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
         }
     }
     // 3-5. Alfven and entropy fields
@@ -415,25 +509,41 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #pragma unroll
         for (int f = 0; f < 3; f++) {
             const int s = 2 * f + 1;
-            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, e.lam[s]));
+            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
         }
     }
-    // 6. back-projection: sum_s r_s corr_s in primitive variables, then dU/dW
+#endif
+    // 6. back-projection: sum_s r_s corr_s in primitive variables, then dU/dW,
+    // added to the central flux (-F_{i-1} + 7F_i + 7F_{i+1} - F_{i+2}) / 12
+    const T alf = bp[BP_ALF * bstride], als = bp[BP_ALS * bstride];
+    const T afcf = bp[BP_AFCF * bstride], ascs = bp[BP_ASCS * bstride];
     const T Fp = corr[6] + corr[0], Fm = corr[6] - corr[0];
     const T Sp = corr[4] + corr[2], Sm = corr[4] - corr[2];
     const T Ap = corr[5] + corr[1], Am = corr[5] - corr[1];
-    const T fs = e.alf * Fp + e.als * Sp;
+    const T fs = alf * Fp + als * Sp;
     const T drho = e.rho * fs + corr[3];
-    const T du = e.alf * e.cf * Fm + e.als * e.cs * Sm;
-    const T dvpar = e.S * (e.alf * e.cf * Sm - e.als * e.cs * Fm);
+    const T du = afcf * Fm + ascs * Sm;
+    const T dvpar = afcf * Sm - ascs * Fm;     // times sgn(B_n), folded into Ssr below
     const T dvperp = Ap;
-    const T dbpar = e.a * e.sr * (e.als * Fp - e.alf * Sp);
-    const T dbperp = -e.S * e.sr * Am;
-    const T dp = e.rho * e.a2 * fs;
-    const T dv1 = e.be1 * dvpar - e.be2 * dvperp;
-    const T dv2 = e.be2 * dvpar + e.be1 * dvperp;
+    const T dbpar = bp[BP_ASR * bstride] * (als * Fp - alf * Sp);
+    const T ssr = bp[BP_SSR * bstride];
+    const T S = ssr < T(0) ? T(-1) : T(1);
+    const T dbperp = -ssr * Am;
+    const T dp = bp[BP_RA2 * bstride] * fs;
+    const T dv1 = e.be1 * S * dvpar - e.be2 * dvperp;
+    const T dv2 = e.be2 * S * dvpar + e.be1 * dvperp;
     const T db1 = e.be1 * dbpar - e.be2 * dbperp;
     const T db2 = e.be2 * dbpar + e.be1 * dbperp;
+    {
+        T f1[7], f2[7], f3[7], f4[7];
+        load7(sm, nc, SF, id[1], f1);
+        load7(sm, nc, SF, id[2], f2);
+        load7(sm, nc, SF, id[3], f3);
+        load7(sm, nc, SF, id[4], f4);
+#pragma unroll
+        for (int f = 0; f < 7; f++)
+            out[f] = (T(7) * (f2[f] + f3[f]) - (f1[f] + f4[f])) * T(1.0 / 12.0);
+    }
     out[0] += drho;
     out[1] += e.u * drho + e.rho * du;
     out[2] += e.v1 * drho + e.rho * dv1;
@@ -441,17 +551,31 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
     out[4] += db1;
     out[5] += db2;
     out[6] += e.hv2 * drho + e.rho * (e.u * du + e.v1 * dv1 + e.v2 * dv2)
-            + e.b1 * db1 + e.b2 * db2 + dp / e.gm1;
+            + e.b1 * db1 + e.b2 * db2 + dp * bp[BP_IGM1 * bstride];
 }
 
 // ---- the kernel -------------------------------------------------------------
+// Tile shapes (interfaces along the axis x pencils, 256 threads) and the
+// number of resident blocks per SM the FP32 register budget is shaped for.
+#ifndef WB_SWEEP_TA_X
+#define WB_SWEEP_TA_X 32
+#endif
+#ifndef WB_SWEEP_TA_YZ
+#define WB_SWEEP_TA_YZ 16
+#endif
+#ifndef WB_SWEEP_MINB_F32
+#define WB_SWEEP_MINB_F32 2
+#endif
 template <int AXIS> struct Shape;
-template <> struct Shape<0> { static constexpr int TA = 32, TP = 8; };
-template <> struct Shape<1> { static constexpr int TA = 8, TP = 32; };
-template <> struct Shape<2> { static constexpr int TA = 8, TP = 32; };
+template <> struct Shape<0> { static constexpr int TA = WB_SWEEP_TA_X, TP = 256 / WB_SWEEP_TA_X; };
+template <> struct Shape<1> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256 / WB_SWEEP_TA_YZ; };
+template <> struct Shape<2> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256 / WB_SWEEP_TA_YZ; };
+
+template <class T> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB_F32; };
 
 template <class T, int AXIS>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A) {
     constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
     constexpr int NS = TA + 5;
     constexpr int NC = NS * TP;
@@ -465,22 +589,34 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
 
     // staging: cells tile.y-3 .. tile.y+TA+1 along the axis, TP pencils
-    for (int e = tid; e < NC; e += TA * TP) {
+    constexpr int NIT = (NC + TA * TP - 1) / (TA * TP);
+    RawCell<T> raw[NIT];
+    long long rc[NIT];
+    int ridx[NIT];
+    bool rok[NIT], rown[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+        const int e = tid + it * TA * TP;
         int s, tp;
         if (AXIS == 0) { tp = e / NS; s = e - tp * NS; }
         else { s = e / TP; tp = e - s * TP; }
         const int cp = tile.z + tp;
-        if (cp >= np) continue;
-        const int raw = tile.y - 3 + s;
-        const int ca = wrap(raw, na);
-        int i, j, k;
-        if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
-        else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
-        else { i = cp; j = tile.w; k = ca; }
-        const bool own = raw >= tile.y && raw < tile.y + TA && raw < na;
-        const int idx = AXIS == 0 ? tp * NS + s : s * TP + tp;
-        stage_cell<T, AXIS>(A, P, i, j, k, sm, NC, idx, own && A.er != nullptr);
+        rok[it] = e < NC && cp < np;
+        const int raw_a = tile.y - 3 + s;
+        rown[it] = raw_a >= tile.y && raw_a < tile.y + TA && raw_a < na;
+        ridx[it] = AXIS == 0 ? tp * NS + s : s * TP + tp;
+        if (rok[it]) {
+            const int ca = wrap(raw_a, na);
+            int i, j, k;
+            if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
+            else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
+            else { i = cp; j = tile.w; k = ca; }
+            load_cell<T>(A, P, i, j, k, raw[it], rc[it]);
+        }
     }
+#pragma unroll
+    for (int it = 0; it < NIT; it++)
+        if (rok[it]) derive_cell<T, AXIS>(A, raw[it], rc[it], sm, NC, ridx[it], rown[it] && A.er != nullptr);
     __syncthreads();
 
     const int ta = AXIS == 0 ? threadIdx.x : threadIdx.y;
@@ -491,7 +627,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
 #pragma unroll
     for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
     T F[7];
-    interface_flux<T>(sm, NC, id, T(A.gamma), F);
+    T* bp = sm + kNSlot * NC + tid;      // this thread's back-projection slots
+    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, F);
 
     // rotate back and store at the lower face of cell ia
     int i, j, k;
@@ -516,16 +653,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
 
 template <class T, int AXIS>
 constexpr size_t smem_bytes() {
-    return sizeof(T) * kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP;
+    return sizeof(T) * (kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP
+                        + kNBack * Shape<AXIS>::TA * Shape<AXIS>::TP);
 }
 
 }  // namespace
-
-void sweep_tile_shape(int axis, int* ta, int* tp) {
-    if (axis == 0) { *ta = Shape<0>::TA; *tp = Shape<0>::TP; }
-    else if (axis == 1) { *ta = Shape<1>::TA; *tp = Shape<1>::TP; }
-    else { *ta = Shape<2>::TA; *tp = Shape<2>::TP; }
-}
 
 template <class T>
 cudaError_t prepare_sweep_kernels() {
@@ -543,16 +675,170 @@ cudaError_t prepare_sweep_kernels() {
 template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    const dim3 block(32, 8);
-    if (axis == 0) sweep_kernel<T, 0><<<ntiles, block, smem_bytes<T, 0>(), s>>>(a);
-    else if (axis == 1) sweep_kernel<T, 1><<<ntiles, block, smem_bytes<T, 1>(), s>>>(a);
-    else sweep_kernel<T, 2><<<ntiles, block, smem_bytes<T, 2>(), s>>>(a);
+    if (axis == 0) sweep_kernel<T, 0><<<ntiles, dim3(Shape<0>::TA, Shape<0>::TP), smem_bytes<T, 0>(), s>>>(a);
+    else if (axis == 1) sweep_kernel<T, 1><<<ntiles, dim3(Shape<1>::TP, Shape<1>::TA), smem_bytes<T, 1>(), s>>>(a);
+    else sweep_kernel<T, 2><<<ntiles, dim3(Shape<2>::TP, Shape<2>::TA), smem_bytes<T, 2>(), s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t prepare_sweep_kernels<float>();
-template cudaError_t prepare_sweep_kernels<double>();
-template cudaError_t launch_sweep<float>(int, const SweepArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_sweep<double>(int, const SweepArgs<double>&, int, cudaStream_t);
+}  // namespace wb
+
+// ---- training-record harvest -------------------------------------------------
+// For each sampled interface (the lower face of cell `cells[t]` along `axis`
+// of patch 0) and each characteristic field and side, one record of
+// WB_MLP_RECORD floats: field, x[6], q[3], T, flag.  v is the split flux g+
+// over the stencil cells i-2..i+3 ('-' side: g- reversed), x = (v - mean) /
+// (max|v - mean| + 1e-12), q the three third-order candidate reconstructions
+// of v at the face, T the face value of the split flux built from hU, hF (the
+// exact face reconstructions of U and F, supplied by the caller) with the
+// same left eigenvector and Lax-Friedrichs speed, q and T normalised like x;
+// flag = 1 when the jump detector (largest of the four differences phi_N
+// reads above kappa times the mean of the other three) or the pressure
+// detector (max p > (1 + pjump) min p over the six cells) fires.
+namespace wb {
+namespace {
+
+template <class T>
+struct HarvestArgs {
+    const T* src;
+    long long ncells;
+    PatchDev P;
+    int axis;
+    const long long* cells;
+    long long n;
+    const double* hU;
+    const double* hF;
+    double gamma, kappa, pjump;
+    float* out;
+};
+
+template <class T, int AXIS>
+__device__ void harvest_one(const HarvestArgs<T>& H, long long t, T* sm, int nc, int base, T* bp,
+                            int bstride) {
+    const PatchDev& P = H.P;
+    const long long cell = H.cells[t];
+    const int i0 = (int)(cell % P.nx), j0 = (int)((cell / P.nx) % P.ny), k0 = (int)(cell / ((long long)P.nx * P.ny));
+    SweepArgs<T> A;
+    A.src = H.src; A.flux = nullptr; A.er = nullptr; A.tiles = nullptr; A.patches = nullptr;
+    A.ncells = H.ncells; A.gamma = H.gamma;
+    const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
+    const int a0 = AXIS == 0 ? i0 : (AXIS == 1 ? j0 : k0);
+    T pmin = T(1e300), pmax = T(-1e300);
+    int id[6];
+    for (int m = 0; m < 6; m++) {
+        const int a = wrap(a0 - 3 + m, na);
+        int i = i0, j = j0, k = k0;
+        if (AXIS == 0) i = a; else if (AXIS == 1) j = a; else k = a;
+        RawCell<T> r;
+        long long c;
+        load_cell<T>(A, P, i, j, k, r, c);
+        id[m] = base + m;
+        derive_cell<T, AXIS>(A, r, c, sm, nc, id[m], false);
+        const T p = sm[SP_P * nc + id[m]];
+        pmin = p < pmin ? p : pmin;
+        pmax = p > pmax ? p : pmax;
+    }
+    const bool pfire = pmax > (T(1) + T(H.pjump)) * pmin;
+    Eig<T> e;
+    {
+        const int l = id[2], r = id[3];
+        const T h = T(0.5);
+        eigen<T>(h * (sm[SU * nc + l] + sm[SU * nc + r]), h * (sm[SP_U * nc + l] + sm[SP_U * nc + r]),
+                 h * (sm[SP_V1 * nc + l] + sm[SP_V1 * nc + r]), h * (sm[SP_V2 * nc + l] + sm[SP_V2 * nc + r]),
+                 h * (sm[SP_BN * nc + l] + sm[SP_BN * nc + r]), h * (sm[(SU + 4) * nc + l] + sm[(SU + 4) * nc + r]),
+                 h * (sm[(SU + 5) * nc + l] + sm[(SU + 5) * nc + r]), h * (sm[SP_P * nc + l] + sm[SP_P * nc + r]),
+                 T(H.gamma), e, bp, bstride);
+    }
+    T hu[7], hf[7];
+    for (int f = 0; f < 7; f++) { hu[f] = T(H.hU[t * 7 + f]); hf[f] = T(H.hF[t * 7 + f]); }
+    for (int G = 0; G < 4; G++) {
+        T w[2][6], g[2][6], tu[2], tf[2];
+        for (int m = 0; m < 6; m++) {
+            T x[7], o[2];
+            load7(sm, nc, SU, id[m], x);
+            if (G == 0) project_pair<0>(e, x, o); else if (G == 1) project_pair<1>(e, x, o);
+            else if (G == 2) project_pair<2>(e, x, o); else project_pair<3>(e, x, o);
+            w[0][m] = o[0]; w[1][m] = o[1];
+            load7(sm, nc, SF, id[m], x);
+            if (G == 0) project_pair<0>(e, x, o); else if (G == 1) project_pair<1>(e, x, o);
+            else if (G == 2) project_pair<2>(e, x, o); else project_pair<3>(e, x, o);
+            g[0][m] = o[0]; g[1][m] = o[1];
+        }
+        {
+            T o[2];
+            if (G == 0) project_pair<0>(e, hu, o); else if (G == 1) project_pair<1>(e, hu, o);
+            else if (G == 2) project_pair<2>(e, hu, o); else project_pair<3>(e, hu, o);
+            tu[0] = o[0]; tu[1] = o[1];
+            if (G == 0) project_pair<0>(e, hf, o); else if (G == 1) project_pair<1>(e, hf, o);
+            else if (G == 2) project_pair<2>(e, hf, o); else project_pair<3>(e, hf, o);
+            tf[0] = o[0]; tf[1] = o[1];
+        }
+        const int sl[2] = {G == 0 ? 0 : (G == 1 ? 2 : (G == 2 ? 1 : 3)), G == 0 ? 6 : (G == 1 ? 4 : (G == 2 ? 5 : 3))};
+        const int nsl = G == 3 ? 1 : 2;
+        for (int q = 0; q < nsl; q++) {
+            const int s = sl[q];
+            const T al = lf_speed(sm, nc, id, s, lam_avg(e, s));
+            for (int side = 0; side < 2; side++) {
+                const T sg = side == 0 ? T(1) : T(-1);
+                T v[6];
+                for (int m = 0; m < 6; m++) {
+                    const int mm = side == 0 ? m : 5 - m;
+                    v[m] = T(0.5) * (g[q][mm] + sg * al * w[q][mm]);
+                }
+                const T Tg = T(0.5) * (tf[q] + sg * al * tu[q]);
+                T mean = T(0);
+                for (int m = 0; m < 6; m++) mean += v[m];
+                mean *= T(1.0 / 6.0);
+                T mx = T(0);
+                for (int m = 0; m < 6; m++) { const T d = tabs(v[m] - mean); mx = d > mx ? d : mx; }
+                const T inv = T(1) / (mx + T(1e-12));
+                T D[4];
+                for (int m = 0; m < 4; m++) D[m] = tabs(v[m + 1] - v[m]);
+                T dmax = D[0], dsum = D[0];
+                for (int m = 1; m < 4; m++) { dmax = D[m] > dmax ? D[m] : dmax; dsum += D[m]; }
+                const bool jfire = dmax > T(H.kappa) * (dsum - dmax) * T(1.0 / 3.0) + T(1e-300);
+                float* o = H.out + ((t * 7 + s) * 2 + side) * WB_MLP_RECORD;
+                o[0] = float(s);
+                for (int m = 0; m < 6; m++) o[1 + m] = float((v[m] - mean) * inv);
+                const T q0 = (T(2) * v[0] - T(7) * v[1] + T(11) * v[2]) * T(1.0 / 6.0);
+                const T q1 = (-v[1] + T(5) * v[2] + T(2) * v[3]) * T(1.0 / 6.0);
+                const T q2 = (T(2) * v[2] + T(5) * v[3] - v[4]) * T(1.0 / 6.0);
+                o[7] = float((q0 - mean) * inv);
+                o[8] = float((q1 - mean) * inv);
+                o[9] = float((q2 - mean) * inv);
+                o[10] = float((Tg - mean) * inv);
+                o[11] = (jfire || pfire) ? 1.f : 0.f;
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32) harvest_kernel(const HarvestArgs<T> H) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int nc = 6 * 32;
+    T* bp = sm + kNSlot * nc + threadIdx.x;
+    const long long t = (long long)blockIdx.x * 32 + threadIdx.x;
+    if (t >= H.n) return;
+    const int base = threadIdx.x * 6;
+    if (H.axis == 0) harvest_one<T, 0>(H, t, sm, nc, base, bp, 32);
+    else if (H.axis == 1) harvest_one<T, 1>(H, t, sm, nc, base, bp, 32);
+    else harvest_one<T, 2>(H, t, sm, nc, base, bp, 32);
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, int axis,
+                           const long long* cells, long long n, const double* hU, const double* hF,
+                           double gamma, double kappa, double pjump, float* out, cudaStream_t s) {
+    HarvestArgs<T> H{src, ncells, P, axis, cells, n, hU, hF, gamma, kappa, pjump, out};
+    const size_t smem = sizeof(T) * (kNSlot * 6 * 32 + kNBack * 32);
+    cudaError_t e = cudaFuncSetAttribute(harvest_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    harvest_kernel<T><<<(unsigned)((n + 31) / 32), 32, smem, s>>>(H);
+    return cudaGetLastError();
+}
 
 }  // namespace wb

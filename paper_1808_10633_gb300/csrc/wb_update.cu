@@ -3,17 +3,22 @@
 // constrained transport of the face-centred field on the staggered mesh
 // (Sec. 2.1), and the Runge-Kutta stage combination.
 //
-// One thread per cell.  It updates the cell's (rho, m, E) and its three
-// lower faces (bx at i-1/2, by at j-1/2, bz at k-1/2).  The nine edge EMFs
-// around those faces are formed from the stored face fluxes:
+// Two kernels per stage.  emf_kernel: one thread per cell forms the three
+// edge EMFs at the cell's own edge index (E_x at (i, j-1/2, k-1/2), E_y at
+// (i-1/2, j, k-1/2), E_z at (i-1/2, j-1/2, k)), each from the stored face
+// fluxes:
 //   E_z(i-1/2, j-1/2) from -F_x(B_y) on the two x faces and F_y(B_x) on the
 //   two y faces next to the edge, and cyclically for E_x, E_y;
 //   emf_mode 0: E = 1/2 (sum of the 4 face values) - 1/4 (sum of the 4 cell
 //   values of -v x B), which reduces to the 1-D upwind flux for flow that
 //   does not vary across the edge; emf_mode 1: E = 1/4 (sum of the 4 face
 //   values).
-// Face rates are -curl E by Stokes' theorem on each face, so the face
-// divergence of b is unchanged to round-off.
+// update_kernel: one thread per cell updates the cell's (rho, m, E) and its
+// three lower faces (bx at i-1/2, by at j-1/2, bz at k-1/2).  Face rates are
+// -curl E by Stokes' theorem on each face (four edge EMFs per face), so the
+// face divergence of b is unchanged to round-off.  Forming every EMF once
+// (instead of nine times per cell inside the update) keeps the update's loads
+// few and independent, so it runs near HBM bandwidth.
 #include "wb_internal.h"
 
 namespace wb {
@@ -102,7 +107,25 @@ __device__ __forceinline__ T combine(const UpdateArgs<T>& A, long long o, T L, T
 }
 
 template <class T>
-__global__ void __launch_bounds__(kCellBlock) update_kernel(const UpdateArgs<T> A) {
+__global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) {
+    const CellBlock cb = A.blocks[blockIdx.x];
+    const Geo<T> G{A.patches[cb.x]};
+    const int local = cb.y + threadIdx.x;
+    const int nxy = G.P.nx * G.P.ny;
+    if (local >= nxy * G.P.nz) return;
+    const int k = local / nxy;
+    const int rem = local - k * nxy;
+    const int j = rem / G.P.nx;
+    const int i = rem - j * G.P.nx;
+    const long long N = A.ncells;
+    const long long c = G.P.off + local;
+    A.emf[c] = emf_x(A, G, i, j, k);
+    A.emf[N + c] = emf_y(A, G, i, j, k);
+    A.emf[2 * N + c] = emf_z(A, G, i, j, k);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
     const Geo<T> G{A.patches[cb.x]};
     const int local = cb.y + threadIdx.x;
@@ -134,13 +157,13 @@ __global__ void __launch_bounds__(kCellBlock) update_kernel(const UpdateArgs<T> 
         A.dst[o + c] = combine(A, o + c, L, dt);
     }
     // faces: -curl E
-    const int ip = inc(i, G.P.nx), jp = inc(j, G.P.ny), kp = inc(k, G.P.nz);
-    const T ez = emf_z(A, G, i, j, k);
-    const T ey = emf_y(A, G, i, j, k);
-    const T ex = emf_x(A, G, i, j, k);
-    const T Lbx = -((emf_z(A, G, i, jp, k) - ez) * idy - (emf_y(A, G, i, j, kp) - ey) * idz);
-    const T Lby = -((emf_x(A, G, i, j, kp) - ex) * idz - (emf_z(A, G, ip, j, k) - ez) * idx);
-    const T Lbz = -((emf_y(A, G, ip, j, k) - ey) * idx - (emf_x(A, G, i, jp, k) - ex) * idy);
+    const T* __restrict__ Ex = A.emf;
+    const T* __restrict__ Ey = A.emf + N;
+    const T* __restrict__ Ez = A.emf + 2 * N;
+    const T ex = Ex[c], ey = Ey[c], ez = Ez[c];
+    const T Lbx = -((Ez[cy] - ez) * idy - (Ey[cz] - ey) * idz);
+    const T Lby = -((Ex[cz] - ex) * idz - (Ez[cx] - ez) * idx);
+    const T Lbz = -((Ey[cx] - ey) * idx - (Ex[cy] - ex) * idy);
     A.dst[5 * N + c] = combine(A, 5 * N + c, Lbx, dt);
     A.dst[6 * N + c] = combine(A, 6 * N + c, Lby, dt);
     A.dst[7 * N + c] = combine(A, 7 * N + c, Lbz, dt);
@@ -149,12 +172,21 @@ __global__ void __launch_bounds__(kCellBlock) update_kernel(const UpdateArgs<T> 
 }  // namespace
 
 template <class T>
+cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    emf_kernel<T><<<nblocks, kCellBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     update_kernel<T><<<nblocks, kCellBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
+template cudaError_t launch_emf<float>(const UpdateArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_emf<double>(const UpdateArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_update<float>(const UpdateArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_update<double>(const UpdateArgs<double>&, int, cudaStream_t);
 

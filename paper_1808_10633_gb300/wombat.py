@@ -26,8 +26,9 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc")
-KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals")
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train")
+MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
+KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
 
 class WombatError(RuntimeError):
@@ -80,6 +81,8 @@ def load() -> ctypes.CDLL:
     L.wb_alu_peak.argtypes = [i, dp]
     L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
+    L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
+    L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
     L.wb_last_error.restype = ctypes.c_char_p
     L.wb_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -234,6 +237,28 @@ def conserved_totals_noalloc(state_ptr: int, precision, ncells: int, dV: float, 
     _check(load().wb_conserved_totals_noalloc(ctypes.c_void_p(state_ptr), int(p), int(ncells),
                                               float(dV), ctypes.c_void_p(out_ptr),
                                               ctypes.c_void_p(int(stream)) if stream else None))
+
+
+def mlp_loss_grad(records: np.ndarray, params: np.ndarray, lam: float):
+    """GPU loss per field and gradient (7, 1379) of the learned-weight networks."""
+    rec = np.ascontiguousarray(records, dtype=np.float32).reshape(-1, MLP_RECORD)
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_NFIELD * MLP_NPARAM)
+    loss = np.empty(MLP_NFIELD)
+    grad = np.empty(MLP_NFIELD * MLP_NPARAM, dtype=np.float32)
+    _check(load().wb_mlp_loss_grad(rec.ctypes.data, rec.shape[0], p.ctypes.data, float(lam),
+                                   loss.ctypes.data, grad.ctypes.data))
+    return loss, grad.reshape(MLP_NFIELD, MLP_NPARAM)
+
+
+def mlp_train(records: np.ndarray, params: np.ndarray, steps: int, batch: int = 4096,
+              lr: float = 1e-3, lam: float = 1e-3, seed: int = 1808):
+    """Adam training on the GPU; returns (params, loss history (steps, 7))."""
+    rec = np.ascontiguousarray(records, dtype=np.float32).reshape(-1, MLP_RECORD)
+    p = np.array(params, dtype=np.float32).reshape(MLP_NFIELD * MLP_NPARAM).copy()
+    hist = np.empty((max(steps, 1), MLP_NFIELD), dtype=np.float32)
+    _check(load().wb_mlp_train(rec.ctypes.data, rec.shape[0], p.ctypes.data, int(steps), int(batch),
+                               float(lr), float(lam), int(seed), hist.ctypes.data))
+    return p.reshape(MLP_NFIELD, MLP_NPARAM), hist[:steps]
 
 
 def version() -> str:
