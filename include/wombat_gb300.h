@@ -245,6 +245,20 @@ int wb_mlp_train(const float *records, long long n, float *params, int steps,
                  int batch, double lr, double lam, unsigned long long seed,
                  float *loss_history);
 
+/* Training records from the solver's own state: for n sampled interfaces
+ * (the lower faces along `axis` of the cells `cells[t]`, host, local indices
+ * of patch 0 of an FP64 grid), WB_MLP_NFIELD x 2 records each (field-major,
+ * '+' side then '-' side) written to records_out (host, n*14*12 floats).
+ * hU, hF (host, n*7 doubles): the exact face reconstructions of the rotated
+ * conservative 7-vector (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and of its
+ * physical flux at each sampled face; they give the targets T through the
+ * same left eigenvectors and Lax-Friedrichs speeds the sweep uses.
+ * kappa, pjump: detector thresholds (records where a detector fires carry
+ * flag 1).  Synchronises.  Errors: WB_EINVAL (not FP64, bad axis/sizes). */
+int wb_harvest(wb_grid *g, int axis, const long long *cells, long long n,
+               const double *hU, const double *hF, double kappa, double pjump,
+               float *records_out);
+
 /* Library version string. */
 const char *wb_version(void);
 

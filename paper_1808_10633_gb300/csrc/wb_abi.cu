@@ -567,6 +567,40 @@ int wb_face_fluxes(wb_grid* g, int axis, double* F_out) {
                                    : face_fluxes_impl<float>(g, axis, F_out);
 }
 
+int wb_harvest(wb_grid* g, int axis, const long long* cells, long long n, const double* hU,
+               const double* hF, double kappa, double pjump, float* records_out) {
+    g_err.clear();
+    if (!g || !cells || !hU || !hF || !records_out || n < 1)
+        return fail(WB_EINVAL, "harvest: null argument or no samples");
+    if (g->precision != WB_FP64) return fail(WB_EINVAL, "harvest: needs an FP64 grid");
+    if (axis < 0 || axis > 2) return fail(WB_EINVAL, "harvest: axis must be 0, 1 or 2");
+    const wb::PatchDev& P = g->h_patches[0];
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    for (long long t = 0; t < n; t++)
+        if (cells[t] < 0 || cells[t] >= np) return fail(WB_EINVAL, "harvest: cell index outside patch 0");
+    WB_CK(cudaSetDevice(g->device));
+    long long* dc = nullptr;
+    double* dh = nullptr;
+    float* dout = nullptr;
+    const size_t nrec = (size_t)n * 14 * WB_MLP_RECORD;
+    cudaError_t e = cudaMalloc(&dc, sizeof(long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(double) * 14 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(float) * nrec);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cells, sizeof(long long) * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dh, hU, sizeof(double) * 7 * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dh + 7 * n, hF, sizeof(double) * 7 * n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = wb::launch_harvest<double>(static_cast<const double*>(g->un), g->N, P, axis, dc, n, dh,
+                                       dh + 7 * n, g->gamma, kappa, pjump, dout, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(records_out, dout, sizeof(float) * nrec, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (dc) cudaFree(dc);
+    if (dh) cudaFree(dh);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(WB_ECUDA, "harvest: %s", cudaGetErrorString(e));
+    return WB_OK;
+}
+
 int wb_sync(wb_grid* g) {
     g_err.clear();
     if (!g) return fail(WB_EINVAL, "null grid");

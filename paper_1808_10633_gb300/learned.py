@@ -1,0 +1,105 @@
+"""Learned WENO weights: training pipeline (data from the solver's own
+states, training with the library's CUDA kernels).
+
+1. Targets.  The flux of eq. FWENO at face i+1/2 is the value there of the
+   function h whose cell average over cell i is the point value F_i (finite
+   differences in the Shu-Osher form).  On a periodic grid h follows from F
+   exactly in Fourier space (h^(k) = F^(k) (theta/2)/sin(theta/2), theta =
+   2 pi k / N, shifted by half a cell): `face_reconstruction`.  This is exact
+   for band-limited data such as the seeded turbulence states.
+2. Records.  `harvest` samples faces of an FP64 grid and lets the library
+   (wb_harvest) project stencils and targets on the interface eigenvectors,
+   split them, normalise them and flag detector hits.
+3. Training.  `train` runs the library's forward/backward/Adam kernels
+   (wb_mlp_train) on the unflagged records.
+
+Parameters are float32 arrays (7, 1379); the layout is in the public header.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import wombat
+
+D_LIN = np.array([0.1, 0.6, 0.3])
+NH, NIN, NOUT = 32, 6, 3
+
+
+def rotated_state_and_flux(U, gamma, axis):
+    """Rotated conservative 7-vector (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and
+    its physical flux along `axis` (0 x, 1 y, 2 z) for cell arrays U[8, ...]
+    whose B entries hold the cell field."""
+    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
+    rho, E = U[0], U[7]
+    mn, m1, m2 = U[1 + n], U[1 + t1], U[1 + t2]
+    bn, b1, b2 = U[4 + n], U[4 + t1], U[4 + t2]
+    u, v1, v2 = mn / rho, m1 / rho, m2 / rho
+    bb = bn * bn + b1 * b1 + b2 * b2
+    p = (gamma - 1.0) * (E - 0.5 * (mn * u + m1 * v1 + m2 * v2) - 0.5 * bb)
+    pt = p + 0.5 * bb
+    X = np.stack([rho, mn, m1, m2, b1, b2, E])
+    F = np.stack([mn, mn * u + pt - bn * bn, m1 * u - bn * b1, m2 * u - bn * b2,
+                  u * b1 - v1 * bn, u * b2 - v2 * bn, (E + pt) * u - bn * (u * bn + v1 * b1 + v2 * b2)])
+    return X, F
+
+
+def face_reconstruction(f, npaxis):
+    """Exact face values h_{i+1/2} (upper face of cell i) along numpy axis
+    `npaxis` of periodic point values f whose cell averages h reproduce."""
+    g = np.moveaxis(f, npaxis, -1)
+    N = g.shape[-1]
+    k = np.arange(N // 2 + 1)
+    th = 2.0 * np.pi * k / N
+    with np.errstate(divide="ignore", invalid="ignore"):
+        fac = np.where(th == 0.0, 1.0, (th / 2.0) / np.sin(th / 2.0))
+    fac = fac * np.exp(0.5j * th)
+    if N % 2 == 0:
+        fac[-1] = 0.0            # Nyquist mode: no real half-cell shift
+    h = np.fft.irfft(np.fft.rfft(g, axis=-1) * fac, n=N, axis=-1)
+    return np.moveaxis(h, -1, npaxis)
+
+
+def harvest(st, nsamples: int, seed: int = 1808, kappa: float = 4.0, pjump: float = 0.5,
+            axes=(0, 1, 2)):
+    """Records (m, 12) from nsamples random faces per axis of state `st`
+    (an inputs.State), computed by the library on an FP64 grid."""
+    rng = np.random.default_rng(seed)
+    g = wombat.Grid.from_state(st, precision="fp64")
+    nx, ny, nz = st.dims
+    out = []
+    for axis in axes:
+        X, F = rotated_state_and_flux(st.U, st.gamma, axis)
+        npax = {0: -1, 1: -2, 2: -3}[axis]
+        hX = face_reconstruction(X, npax)
+        hF = face_reconstruction(F, npax)
+        idx = rng.integers(0, [nx, ny, nz], size=(nsamples, 3))
+        cells = (idx[:, 2] * ny + idx[:, 1]) * nx + idx[:, 0]
+        low = idx.copy()                                  # lower face of cell = upper face of cell - e
+        low[:, axis] = (low[:, axis] - 1) % (nx, ny, nz)[axis]
+        hu = hX[:, low[:, 2], low[:, 1], low[:, 0]].T
+        hf = hF[:, low[:, 2], low[:, 1], low[:, 0]].T
+        out.append(g.harvest(axis, cells, hu, hf, kappa, pjump).reshape(-1, wombat.MLP_RECORD))
+    g.close()
+    return np.concatenate(out)
+
+
+def init_params(seed: int = 1808):
+    """Small random hidden layers and an output layer that starts at the
+    linear weights (W3 = 0, b3 = log d)."""
+    rng = np.random.default_rng(seed)
+    P = []
+    for _ in range(wombat.MLP_NFIELD):
+        W1 = rng.standard_normal((NH, NIN)) * np.sqrt(1.0 / NIN)
+        W2 = rng.standard_normal((NH, NH)) * np.sqrt(1.0 / NH)
+        W3 = np.zeros((NOUT, NH))
+        P.append(np.concatenate([W1.ravel(), np.zeros(NH), W2.ravel(), np.zeros(NH), W3.ravel(),
+                                 np.log(D_LIN)]))
+    return np.array(P, dtype=np.float32)
+
+
+def train(records, params=None, steps: int = 2000, batch: int = 4096, lr: float = 2e-3,
+          lam: float = 1e-3, seed: int = 1808):
+    """Adam on the GPU; returns (params (7, 1379), loss history (steps, 7))."""
+    if params is None:
+        params = init_params(seed)
+    return wombat.mlp_train(records, params, steps, batch, lr, lam, seed)

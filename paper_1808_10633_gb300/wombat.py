@@ -26,7 +26,7 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train")
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
     L.wb_alu_peak.argtypes = [i, dp]
     L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
+    L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
     L.wb_last_error.restype = ctypes.c_char_p
@@ -202,6 +203,17 @@ class Grid:
         out = np.empty(7 * self.ncells)
         _check(self._lib.wb_face_fluxes(self._h, int(axis), out.ctypes.data))
         return out.reshape(7, self.ncells)
+
+    def harvest(self, axis: int, cells, hU, hF, kappa: float = 4.0, pjump: float = 0.5):
+        """Training records (n, 14, 12) for the lower faces of `cells` along axis."""
+        c = np.ascontiguousarray(cells, dtype=np.int64)
+        hu = np.ascontiguousarray(hU, dtype=np.float64).reshape(-1, 7)
+        hf = np.ascontiguousarray(hF, dtype=np.float64).reshape(-1, 7)
+        assert hu.shape[0] == c.size == hf.shape[0]
+        out = np.empty((c.size, 14, MLP_RECORD), dtype=np.float32)
+        _check(self._lib.wb_harvest(self._h, int(axis), c.ctypes.data, c.size, hu.ctypes.data,
+                                    hf.ctypes.data, float(kappa), float(pjump), out.ctypes.data))
+        return out
 
     def sync(self):
         _check(self._lib.wb_sync(self._h))

@@ -1,0 +1,140 @@
+"""Learned WENO weights on the GPU: the library's forward/backward kernels
+against the FP64 CPU backprop (oracle/learned.py), harvested training records
+against an oracle recomputation, and training that lowers the loss."""
+import numpy as np
+import pytest
+
+from paper_1808_10633_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wb():
+    from paper_1808_10633_gb300 import build, wombat
+
+    build.build()
+    return wombat
+
+
+def _records(n, seed):
+    from oracle import learned as Lr
+
+    rng = np.random.default_rng(seed)
+    rec = np.zeros((n, 12), dtype=np.float32)
+    rec[:, 0] = rng.integers(0, 7, n)
+    rec[:, 1:7] = Lr.normalise(rng.standard_normal((n, 6)))
+    q = Lr.candidates(rng.standard_normal((n, 5)))
+    rec[:, 7:10] = q
+    rec[:, 10] = q @ Lr.D_LIN + 0.1 * rng.standard_normal(n)
+    rec[:, 11] = (rng.uniform(size=n) < 0.1)          # some flagged records
+    return rec
+
+
+def test_mlp_gradient_matches_fp64_backprop(wb):
+    from oracle import learned as Lr
+
+    rng = np.random.default_rng(7)
+    params = (rng.standard_normal((7, Lr.NPARAM)) * 0.3).astype(np.float32)
+    rec = _records(3000, 8)
+    lam = 1e-2
+    loss, grad = wb.mlp_loss_grad(rec, params, lam)
+    for f in range(7):
+        sel = (rec[:, 0] == f) & (rec[:, 11] == 0)
+        L, g = Lr.loss_and_grad(params[f].astype(np.float64), rec[sel, 1:7].astype(np.float64),
+                                rec[sel, 7:10].astype(np.float64), rec[sel, 10].astype(np.float64), lam)
+        assert loss[f] == pytest.approx(L, rel=1e-4)
+        assert np.abs(grad[f] - g).max() <= 1e-3 * np.abs(g).max(), f
+
+
+def _oracle_records(orc, st, axis, cell_ijk, hu, hf, kappa, pjump):
+    """Records of one face recomputed with the oracle's eigen-system."""
+    from oracle import learned as Lr
+
+    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
+    perm = [0, 1 + n, 1 + t1, 1 + t2, 4 + n, 4 + t1, 4 + t2, 7]
+    SYS = [0, 1, 2, 3, 5, 6, 7]
+    nx, ny, nz = st.dims
+    dims = (nx, ny, nz)
+    i, j, k = cell_ijk
+    Us = np.empty((6, 8))
+    for m in range(6):
+        q = [i, j, k]
+        q[axis] = (q[axis] + m - 3) % dims[axis]
+        Us[m] = st.U[perm, q[2], q[1], q[0]]
+    W = np.array([orc.cons_to_prim(u, st.gamma) for u in Us])
+    F = np.array([orc.flux_n(u, st.gamma) for u in Us])
+    lk = []
+    for kk in range(6):
+        cf, ca, cs = orc.wave_speeds(W[kk], st.gamma)
+        u = W[kk][1]
+        lk.append([u - cf, u - ca, u - cs, u, u + cs, u + ca, u + cf])
+    lk = np.array(lk)
+    lam, RU, LU, _ = orc.eigen(0.5 * (W[2] + W[3]), st.gamma)
+    pfire = W[:, 7].max() > (1 + pjump) * W[:, 7].min()
+    out = np.empty((7, 2, 12))
+    for s in range(7):
+        al = max(abs(lam[s]), np.abs(lk[:, s]).max())
+        w = Us[:, SYS] @ LU[s]
+        g = F[:, SYS] @ LU[s]
+        tu, tf = LU[s] @ hu, LU[s] @ hf
+        for side, sg in ((0, 1.0), (1, -1.0)):
+            v = 0.5 * (g + sg * al * w)
+            if side == 1:
+                v = v[::-1]
+            Tg = 0.5 * (tf + sg * al * tu)
+            mean = v.mean()
+            inv = 1.0 / (np.abs(v - mean).max() + 1e-12)
+            qq = Lr.candidates(v[:5])
+            D = np.diff(v)[:4]
+            out[s, side, 0] = s
+            out[s, side, 1:7] = (v - mean) * inv
+            out[s, side, 7:10] = (qq - mean) * inv
+            out[s, side, 10] = (Tg - mean) * inv
+            out[s, side, 11] = float(pfire or Lr.detector(D[None, :], kappa)[0])
+    return out
+
+
+def test_harvest_records_match_oracle(orc, wb):
+    from paper_1808_10633_gb300 import learned as Ln
+
+    st = I.turbulence(24, seed=5)
+    st = I.add_blasts(st, nblast=4, rmin=0.1, rmax=0.15)     # some detector hits
+    g = wb.Grid.from_state(st, precision="fp64")
+    rng = np.random.default_rng(3)
+    nx, ny, nz = st.dims
+    nflag = 0
+    for axis in range(3):
+        X, F = Ln.rotated_state_and_flux(st.U, st.gamma, axis)
+        npax = {0: -1, 1: -2, 2: -3}[axis]
+        hX, hF = Ln.face_reconstruction(X, npax), Ln.face_reconstruction(F, npax)
+        idx = rng.integers(0, [nx, ny, nz], size=(12, 3))
+        low = idx.copy()
+        low[:, axis] = (low[:, axis] - 1) % (nx, ny, nz)[axis]
+        hu = hX[:, low[:, 2], low[:, 1], low[:, 0]].T
+        hf = hF[:, low[:, 2], low[:, 1], low[:, 0]].T
+        cells = (idx[:, 2] * ny + idx[:, 1]) * nx + idx[:, 0]
+        rec = g.harvest(axis, cells, hu, hf, 4.0, 0.5).reshape(12, 7, 2, 12)
+        for t in range(12):
+            ref = _oracle_records(orc, st, axis, idx[t], hu[t], hf[t], 4.0, 0.5)
+            assert np.array_equal(rec[t, :, :, 0], ref[:, :, 0])
+            assert np.abs(rec[t, :, :, 1:11] - ref[:, :, 1:11]).max() < 2e-3, (axis, t)
+            mism = (rec[t, :, :, 11] != ref[:, :, 11]).sum()
+            assert mism <= 1, (axis, t, mism)
+            nflag += int(ref[:, :, 11].sum())
+    g.close()
+    assert nflag > 0
+
+
+def test_training_lowers_the_loss(wb):
+    from paper_1808_10633_gb300 import learned as Ln
+
+    st = I.turbulence(32, seed=9)
+    rec = Ln.harvest(st, 4000, seed=1)
+    assert rec.shape[1] == 12 and (rec[:, 11] == 0).mean() > 0.5
+    p0 = Ln.init_params(3)
+    loss0, _ = wb.mlp_loss_grad(rec, p0, 1e-3)
+    p, hist = Ln.train(rec, p0, steps=400, batch=2048, lr=2e-3, lam=1e-3, seed=4)
+    loss1, _ = wb.mlp_loss_grad(rec, p, 1e-3)
+    assert np.all(np.isfinite(hist))
+    assert loss1.mean() < 0.9 * loss0.mean(), (loss0, loss1)
