@@ -52,9 +52,12 @@ typedef enum {
 
 typedef enum {
     WB_FP64 = 0,          /* whole path in FP64                               */
-    WB_FP32 = 1           /* state and sweeps in FP32; FP64 in the eigenvector
+    WB_FP32 = 1,          /* state and sweeps in FP32; FP64 in the eigenvector
                              normalisation near degenerate points, the CFL
                              reduction and the conserved totals              */
+    WB_FP32_LEARNED = 2   /* as WB_FP32, with the nonlinear weights of phi_N
+                             from the learned networks (wb_set_mlp) wherever
+                             the detectors do not fire                       */
 } wb_precision;
 
 typedef enum {
@@ -258,6 +261,15 @@ int wb_mlp_train(const float *records, long long n, float *params, int steps,
 int wb_harvest(wb_grid *g, int axis, const long long *cells, long long n,
                const double *hU, const double *hF, double kappa, double pjump,
                float *records_out);
+
+/* Install the learned-weight networks on a WB_FP32_LEARNED grid (required
+ * before its first step).  params: host, WB_MLP_NFIELD * WB_MLP_NPARAM
+ * floats (copied, rounded to BF16 for the tensor cores).  kappa: jump
+ * detector threshold (the largest of the four differences phi_N reads
+ * against kappa times the mean of the other three); pjump: pressure
+ * detector (max p > (1 + pjump) min p over the six stencil cells).  Where a
+ * detector fires the Jiang-Shu weights are used.  Synchronises. */
+int wb_set_mlp(wb_grid *g, const float *params, double kappa, double pjump);
 
 /* Library version string. */
 const char *wb_version(void);

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libwombat_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file extra flags: the FP32 sweep uses fast single-precision division
 # and square root (FP64 code in that file is unaffected)
-EXTRA = {"wb_sweep_f32.cu": ["-use_fast_math"]}
+EXTRA = {"wb_sweep_f32.cu": ["-use_fast_math"], "wb_sweep_learned.cu": ["-use_fast_math"]}
 
 
 def nvcc() -> str:

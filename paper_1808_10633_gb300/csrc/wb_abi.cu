@@ -85,6 +85,8 @@ struct wb_grid {
     void* flux = nullptr;
     void* er = nullptr;
     void* emf = nullptr;
+    uint32_t* d_mlp = nullptr;            // learned weights, fragment order
+    double kappa = 4.0, pjump = 0.5;
     wb::PatchDev* d_patches = nullptr;
     std::vector<wb::PatchDev> h_patches;
     wb::Tile* d_tiles[3] = {nullptr, nullptr, nullptr};
@@ -128,7 +130,15 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.gamma = g->gamma;
             int rc = prof_begin(pf, g->stream);
             if (rc != WB_OK) return rc;
-            WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+            if constexpr (sizeof(T) == 4) {
+                if (g->precision == WB_FP32_LEARNED)
+                    WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
+                                                   (float)g->pjump, g->stream));
+                else
+                    WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+            } else {
+                WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+            }
             if ((rc = prof_end(pf, g->stream, WB_K_SWEEP_X + axis)) != WB_OK) return rc;
         }
         wb::UpdateArgs<T> u;
@@ -228,6 +238,8 @@ int capture_step(wb_grid* g, int mode, double value) {
 }
 
 int run_steps(wb_grid* g, int mode, double value, int nsteps) {
+    if (g->precision == WB_FP32_LEARNED && !g->d_mlp)
+        return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
     WB_CK(cudaSetDevice(g->device));
     int rc = capture_step(g, mode, value);
     if (rc != WB_OK) return rc;
@@ -269,7 +281,7 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_patches, g->d_tiles[0],
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_patches, g->d_tiles[0],
                     g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_scalars, g->d_smax,
                     g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
@@ -298,7 +310,17 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     a.patches = g->d_patches;
     a.ncells = N;
     a.gamma = g->gamma;
-    WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+    if constexpr (sizeof(T) == 4) {
+        if (g->precision == WB_FP32_LEARNED) {
+            if (!g->d_mlp) return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
+            WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
+                                           (float)g->pjump, g->stream));
+        } else {
+            WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+        }
+    } else {
+        WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
+    }
     // 7 N doubles fit the 11 N staging buffer
     WB_CK(wb::launch_export_flux<T>(flux, g->d_io, g->d_blocks, g->d_patches, N, g->nblocks,
                                     g->stream));
@@ -330,7 +352,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (d->ghost != 3) return fail(WB_EINVAL, "ghost must be 3 (WENO5 stencil), got %d", d->ghost);
     if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return fail(WB_EINVAL, "dx, dy, dz must be > 0");
     if (!(d->gamma > 1.0)) return fail(WB_EINVAL, "gamma must be > 1");
-    if (d->precision != WB_FP64 && d->precision != WB_FP32)
+    if (d->precision != WB_FP64 && d->precision != WB_FP32 && d->precision != WB_FP32_LEARNED)
         return fail(WB_EINVAL, "unknown precision %d", d->precision);
     if (d->integrator != WB_SSPRK3 && d->integrator != WB_RK4)
         return fail(WB_EINVAL, "unknown integrator %d", d->integrator);
@@ -437,6 +459,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
         return bail(fail(WB_ECUDA, "memset failed"));
     cudaError_t pe = g->precision == WB_FP64 ? wb::prepare_sweep_kernels<double>()
                                              : wb::prepare_sweep_kernels<float>();
+    if (pe == cudaSuccess && g->precision == WB_FP32_LEARNED) pe = wb::prepare_sweep_learned();
     if (pe != cudaSuccess) return bail(fail(WB_ECUDA, "kernel attributes: %s", cudaGetErrorString(pe)));
     if ((rc = upload(g, U0, b0)) != WB_OK) return bail(rc);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess)
@@ -598,6 +621,30 @@ int wb_harvest(wb_grid* g, int axis, const long long* cells, long long n, const 
     if (dh) cudaFree(dh);
     if (dout) cudaFree(dout);
     if (e != cudaSuccess) return fail(WB_ECUDA, "harvest: %s", cudaGetErrorString(e));
+    return WB_OK;
+}
+
+int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
+    g_err.clear();
+    if (!g || !params) return fail(WB_EINVAL, "null argument");
+    if (g->precision != WB_FP32_LEARNED) return fail(WB_EINVAL, "wb_set_mlp needs a WB_FP32_LEARNED grid");
+    if (!(kappa > 0) || !(pjump > 0)) return fail(WB_EINVAL, "kappa and pjump must be > 0");
+    WB_CK(cudaSetDevice(g->device));
+    const size_t words = wb::mlp_fragment_words();
+    std::vector<uint32_t> frag(words);
+    wb::mlp_fragments(params, frag.data());
+    if (!g->d_mlp) {
+        int rc = dmalloc(g, &g->d_mlp, sizeof(uint32_t) * words);
+        if (rc != WB_OK) return rc;
+    }
+    WB_CK(cudaMemcpyAsync(g->d_mlp, frag.data(), sizeof(uint32_t) * words, cudaMemcpyHostToDevice, g->stream));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    g->kappa = kappa;
+    g->pjump = pjump;
+    if (g->graph) {              // kernel arguments changed: capture again
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
     return WB_OK;
 }
 

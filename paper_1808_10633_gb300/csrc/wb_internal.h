@@ -73,6 +73,12 @@ cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
 template <class T>
 cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
 
+cudaError_t prepare_sweep_learned();
+cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles, const uint32_t* mlp,
+                                 float kappa, float pjump, cudaStream_t s);
+void mlp_fragments(const float* params, uint32_t* out);
+size_t mlp_fragment_words();
+
 template <class T>
 cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, int axis,
                            const long long* cells, long long n, const double* hU, const double* hF,

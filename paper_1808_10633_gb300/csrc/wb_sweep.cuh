@@ -114,6 +114,14 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
     return phi_n(dm4, dm3, dm2, dm1) - phi_n(dp0, dp1, dp2, dp3);
 }
 
+// Weight policy of the classic scheme: Jiang-Shu weights for every field.
+template <class T>
+struct JsWeights {
+    __device__ __forceinline__ T corr(int, const T (&w)[6], const T (&g)[6], T alpha) {
+        return weno_corr<T>(w, g, alpha);
+    }
+};
+
 // Interface eigen-structure: everything the projection and back-projection
 // need, with 1/rho and (gamma-1) folded into the left coefficients.
 template <class T>
@@ -420,9 +428,9 @@ __device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const in
     return al;
 }
 
-template <class T>
+template <class T, class Wt>
 __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc, const int (&id)[6],
-                                               T gamma, T* __restrict__ bp, int bstride,
+                                               T gamma, T* __restrict__ bp, int bstride, Wt& wt,
                                                T (&out)[7]) {
     // 1-2. interface state and eigen-structure
     Eig<T> e;
@@ -464,9 +472,9 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
                 else project_pair<3>(e, x, o);
                 g[0][m] = o[0]; g[1][m] = o[1];
             }
-            corr[s0[G]] = weno_corr<T>(w[0], g[0], lf_speed(sm, nc, id, s0[G], lam_avg(e, s0[G])));
+            corr[s0[G]] = wt.corr(s0[G], w[0], g[0], lf_speed(sm, nc, id, s0[G], lam_avg(e, s0[G])));
             if (G != 3)
-                corr[s1[G]] = weno_corr<T>(w[1], g[1], lf_speed(sm, nc, id, s1[G], lam_avg(e, s1[G])));
+                corr[s1[G]] = wt.corr(s1[G], w[1], g[1], lf_speed(sm, nc, id, s1[G], lam_avg(e, s1[G])));
         }
     }
 #else
@@ -488,7 +496,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #pragma unroll
         for (int f = 0; f < 4; f++) {
             const int s = 2 * f;
-            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
+            corr[s] = wt.corr(s, w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
         }
     }
     // 3-5. Alfven and entropy fields
@@ -509,7 +517,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #pragma unroll
         for (int f = 0; f < 3; f++) {
             const int s = 2 * f + 1;
-            corr[s] = weno_corr<T>(w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
+            corr[s] = wt.corr(s, w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
         }
     }
 #endif
@@ -628,7 +636,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
     T F[7];
     T* bp = sm + kNSlot * NC + tid;      // this thread's back-projection slots
-    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, F);
+    JsWeights<T> js;
+    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, js, F);
 
     // rotate back and store at the lower face of cell ia
     int i, j, k;

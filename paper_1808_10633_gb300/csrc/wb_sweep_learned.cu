@@ -1,0 +1,365 @@
+// wb_sweep_learned.cu -- FP32 WENO5 sweep with learned nonlinear weights.
+//
+// The characteristic sweep of wb_sweep.cuh (Sec. 2.1 eq. FWENO) with one
+// change: for every interface, field and side, the weights (w0, w2) of phi_N
+// come from a small per-field network (6 -> 32 -> 32 -> 3, GELU, softmax)
+// evaluated on the normalised split-flux stencil, unless a detector fires
+// (a jump in the four differences phi_N reads, or a pressure ratio across the
+// six stencil cells), in which case the Jiang-Shu weights are kept.
+//
+// Network evaluation on the tensor cores: all 32 lanes of a warp reach the
+// same field together, so the warp runs the network on a 64 x 6 batch (two
+// sides per lane) with mma.sync.m16n8k8 (first layer, the bias folded in as
+// a seventh input equal to 1) and mma.sync.m16n8k16 (hidden and output
+// layers), BF16 operands and FP32 accumulators.  A layer's accumulator
+// fragments are re-packed in registers as the next layer's A fragments; the
+// weights sit in shared memory already in B-fragment order (34 words per lane
+// per field, written by wb_set_mlp on the host side).  GELU uses the
+// hardware tanh approximation.  Batch rows are independent, so a lane whose
+// interface lies outside the patch still joins the warp-wide products (with
+// a valid stencil) and only skips its store.
+#include "wb_sweep.cuh"
+
+#include <cuda_bf16.h>
+
+namespace wb {
+namespace {
+
+constexpr int kMlpWords = 34;                    // per lane per field
+constexpr int kMlpSmemWords = WB_MLP_NFIELD * kMlpWords * 32;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float gelu_fast(float x) {
+    const float u = 0.7978845608f * (x + 0.044715f * x * x * x);
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return 0.5f * x * (1.0f + t);
+}
+
+// One warp, one field: omega (w0, w2) for the 64 rows of `in` (row r holds 8
+// bf16: x0..x5, 1, 0) into om[2r], om[2r+1].
+__device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const uint32_t* __restrict__ in,
+                                         float* __restrict__ om, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const float* Wf = reinterpret_cast<const float*>(W);
+#pragma unroll 1
+    for (int mt = 0; mt < 4; mt++) {
+        const int r0 = 16 * mt + g, r1 = r0 + 8;
+        const uint32_t a0 = in[r0 * 4 + t], a1 = in[r1 * 4 + t];
+        float c1[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
+            mma_k8(c1[nt], a0, a1, W[nt * 32 + lane]);
+        }
+        uint32_t A2[2][4];
+#pragma unroll
+        for (int kt = 0; kt < 2; kt++) {
+            A2[kt][0] = pack_bf16(gelu_fast(c1[2 * kt][0]), gelu_fast(c1[2 * kt][1]));
+            A2[kt][1] = pack_bf16(gelu_fast(c1[2 * kt][2]), gelu_fast(c1[2 * kt][3]));
+            A2[kt][2] = pack_bf16(gelu_fast(c1[2 * kt + 1][0]), gelu_fast(c1[2 * kt + 1][1]));
+            A2[kt][3] = pack_bf16(gelu_fast(c1[2 * kt + 1][2]), gelu_fast(c1[2 * kt + 1][3]));
+        }
+        float c2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const float blo = Wf[(24 + 2 * nt) * 32 + lane], bhi = Wf[(25 + 2 * nt) * 32 + lane];
+            c2[nt][0] = blo; c2[nt][1] = bhi; c2[nt][2] = blo; c2[nt][3] = bhi;
+#pragma unroll
+            for (int kt = 0; kt < 2; kt++)
+                mma_k16(c2[nt], A2[kt], W[(4 + nt * 4 + kt * 2) * 32 + lane],
+                        W[(5 + nt * 4 + kt * 2) * 32 + lane]);
+        }
+        uint32_t A3[2][4];
+#pragma unroll
+        for (int kt = 0; kt < 2; kt++) {
+            A3[kt][0] = pack_bf16(gelu_fast(c2[2 * kt][0]), gelu_fast(c2[2 * kt][1]));
+            A3[kt][1] = pack_bf16(gelu_fast(c2[2 * kt][2]), gelu_fast(c2[2 * kt][3]));
+            A3[kt][2] = pack_bf16(gelu_fast(c2[2 * kt + 1][0]), gelu_fast(c2[2 * kt + 1][1]));
+            A3[kt][3] = pack_bf16(gelu_fast(c2[2 * kt + 1][2]), gelu_fast(c2[2 * kt + 1][3]));
+        }
+        const float b3lo = Wf[32 * 32 + lane], b3hi = Wf[33 * 32 + lane];
+        float c3[4] = {b3lo, b3hi, b3lo, b3hi};
+#pragma unroll
+        for (int kt = 0; kt < 2; kt++)
+            mma_k16(c3, A3[kt], W[(20 + kt * 2) * 32 + lane], W[(21 + kt * 2) * 32 + lane]);
+        // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1
+        const float z2a = __shfl_down_sync(0xffffffffu, c3[0], 1);
+        const float z2b = __shfl_down_sync(0xffffffffu, c3[2], 1);
+        if (t == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float z0 = h == 0 ? c3[0] : c3[2], z1 = h == 0 ? c3[1] : c3[3];
+                const float z2 = h == 0 ? z2a : z2b;
+                const float zm = fmaxf(z0, fmaxf(z1, z2));
+                const float e0 = __expf(z0 - zm), e1 = __expf(z1 - zm), e2 = __expf(z2 - zm);
+                const float inv = __fdividef(1.0f, e0 + e1 + e2);
+                const int r = h == 0 ? r0 : r1;
+                om[2 * r] = e0 * inv;
+                om[2 * r + 1] = e2 * inv;
+            }
+        }
+    }
+}
+
+// Weight policy of the learned scheme.
+struct LearnedWeights {
+    const uint32_t* W;        // shared, [field][34][32]
+    uint32_t* in;             // shared, this warp's 64 x 4 words
+    float* om;                // shared, this warp's 64 x 2
+    int lane;
+    bool pfire;               // pressure detector of this interface
+    float kappa;
+
+    __device__ __forceinline__ float corr(int s, const float (&w)[6], const float (&g)[6], float alpha) {
+        const float ha = 0.5f * alpha;
+        float vp[6], vm[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            vp[k] = 0.5f * g[k] + ha * w[k];
+            vm[k] = 0.5f * g[5 - k] - ha * w[5 - k];     // '-' side reversed
+        }
+        float Dp[4], Dm[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) { Dp[k] = vp[k + 1] - vp[k]; Dm[k] = vm[k] - vm[k + 1]; }
+        // Dp = (D+_{i-3/2}, .., D+_{i+3/2}); Dm = (D-_{i+5/2}, .., D-_{i-1/2})
+        bool fire[2];
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const float* v = side == 0 ? vp : vm;
+            float mean = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; k++) mean += v[k];
+            mean *= (1.0f / 6.0f);
+            float mx = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; k++) mx = fmaxf(mx, fabsf(v[k] - mean));
+            const float inv = __fdividef(1.0f, mx + 1e-12f);
+            const int r = 2 * lane + side;
+            in[r * 4 + 0] = pack_bf16((v[0] - mean) * inv, (v[1] - mean) * inv);
+            in[r * 4 + 1] = pack_bf16((v[2] - mean) * inv, (v[3] - mean) * inv);
+            in[r * 4 + 2] = pack_bf16((v[4] - mean) * inv, (v[5] - mean) * inv);
+            in[r * 4 + 3] = pack_bf16(1.0f, 0.0f);
+            const float* D = side == 0 ? Dp : Dm;
+            float a[4], dmax = 0.f, dsum = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; k++) { a[k] = fabsf(D[k]); dmax = fmaxf(dmax, a[k]); dsum += a[k]; }
+            fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f;
+        }
+        __syncwarp();
+        mlp_warp(W + s * kMlpWords * 32, in, om, lane);
+        __syncwarp();
+        const float w0p = om[4 * lane], w2p = om[4 * lane + 1];
+        const float w0m = om[4 * lane + 2], w2m = om[4 * lane + 3];
+        __syncwarp();
+        const float php = fire[0] ? phi_n(Dp[0], Dp[1], Dp[2], Dp[3])
+                                  : w0p * (Dp[0] - 2.f * Dp[1] + Dp[2]) * (1.f / 3.f)
+                                        + (w2p - 0.5f) * (Dp[1] - 2.f * Dp[2] + Dp[3]) * (1.f / 6.f);
+        const float phm = fire[1] ? phi_n(Dm[0], Dm[1], Dm[2], Dm[3])
+                                  : w0m * (Dm[0] - 2.f * Dm[1] + Dm[2]) * (1.f / 3.f)
+                                        + (w2m - 0.5f) * (Dm[1] - 2.f * Dm[2] + Dm[3]) * (1.f / 6.f);
+        return phm - php;
+    }
+};
+
+template <int AXIS>
+__global__ void __launch_bounds__(256, 1) sweep_learned_kernel(const SweepArgs<float> A,
+                                                               const uint32_t* __restrict__ mlp,
+                                                               float kappa, float pjump) {
+    using T = float;
+    constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
+    constexpr int NS = TA + 5;
+    constexpr int NC = NS * TP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    uint32_t* Wsm = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNBack * TA * TP));
+    uint32_t* wbuf = Wsm + kMlpSmemWords;                 // 8 warps x (256 + 128) words
+
+    const Tile tile = A.tiles[blockIdx.x];
+    const PatchDev P = A.patches[tile.x];
+    const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
+    const int np = AXIS == 0 ? P.ny : P.nx;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+
+    for (int i = tid; i < kMlpSmemWords; i += TA * TP) Wsm[i] = mlp[i];
+
+    constexpr int NIT = (NC + TA * TP - 1) / (TA * TP);
+    RawCell<T> raw[NIT];
+    long long rc[NIT];
+    int ridx[NIT];
+    bool rok[NIT], rown[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+        const int e = tid + it * TA * TP;
+        int s, tp;
+        if (AXIS == 0) { tp = e / NS; s = e - tp * NS; }
+        else { s = e / TP; tp = e - s * TP; }
+        const int cp = tile.z + tp;
+        rok[it] = e < NC && cp < np;
+        const int raw_a = tile.y - 3 + s;
+        rown[it] = raw_a >= tile.y && raw_a < tile.y + TA && raw_a < na;
+        ridx[it] = AXIS == 0 ? tp * NS + s : s * TP + tp;
+        if (rok[it]) {
+            const int ca = wrap(raw_a, na);
+            int i, j, k;
+            if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
+            else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
+            else { i = cp; j = tile.w; k = ca; }
+            load_cell<T>(A, P, i, j, k, raw[it], rc[it]);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; it++)
+        if (rok[it]) derive_cell<T, AXIS>(A, raw[it], rc[it], sm, NC, ridx[it], rown[it] && A.er != nullptr);
+    __syncthreads();
+
+    const int ta = AXIS == 0 ? threadIdx.x : threadIdx.y;
+    const int tp0 = AXIS == 0 ? threadIdx.y : threadIdx.x;
+    const int ia = tile.y + ta, ip = tile.z + tp0;
+    const bool valid = ia < na && ip < np;
+    const int tp = ip < np ? tp0 : 0;                      // stand-in stencil for idle lanes
+    int id[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
+    float pmin = sm[SP_P * NC + id[0]], pmax = pmin;
+#pragma unroll
+    for (int m = 1; m < 6; m++) {
+        const float p = sm[SP_P * NC + id[m]];
+        pmin = fminf(pmin, p);
+        pmax = fmaxf(pmax, p);
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    LearnedWeights lw{Wsm, wbuf + warp * 384, reinterpret_cast<float*>(wbuf + warp * 384 + 256), lane,
+                      pmax > (1.0f + pjump) * pmin, kappa};
+    T F[7];
+    T* bp = sm + kNSlot * NC + tid;
+    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, lw, F);
+    if (!valid) return;
+
+    int i, j, k;
+    if (AXIS == 0) { i = ia; j = ip; k = tile.w; }
+    else if (AXIS == 1) { i = ip; j = ia; k = tile.w; }
+    else { i = ip; j = tile.w; k = ia; }
+    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
+    const long long N = A.ncells;
+    T* __restrict__ fo = A.flux;
+    T fx, fy, fz;
+    if (AXIS == 0) { fx = F[1]; fy = F[2]; fz = F[3]; }
+    else if (AXIS == 1) { fy = F[1]; fz = F[2]; fx = F[3]; }
+    else { fz = F[1]; fx = F[2]; fy = F[3]; }
+    fo[c] = F[0];
+    fo[N + c] = fx;
+    fo[2 * N + c] = fy;
+    fo[3 * N + c] = fz;
+    fo[4 * N + c] = F[6];
+    fo[5 * N + c] = F[4];
+    fo[6 * N + c] = F[5];
+}
+
+template <int AXIS>
+constexpr size_t learned_smem_bytes() {
+    return smem_bytes<float, AXIS>() + sizeof(uint32_t) * (kMlpSmemWords + 8 * 384);
+}
+
+}  // namespace
+
+cudaError_t prepare_sweep_learned() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(sweep_learned_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)learned_smem_bytes<0>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_learned_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)learned_smem_bytes<1>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_learned_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)learned_smem_bytes<2>());
+}
+
+cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles, const uint32_t* mlp,
+                                 float kappa, float pjump, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (axis == 0)
+        sweep_learned_kernel<0><<<ntiles, dim3(Shape<0>::TA, Shape<0>::TP), learned_smem_bytes<0>(), s>>>(
+            a, mlp, kappa, pjump);
+    else if (axis == 1)
+        sweep_learned_kernel<1><<<ntiles, dim3(Shape<1>::TP, Shape<1>::TA), learned_smem_bytes<1>(), s>>>(
+            a, mlp, kappa, pjump);
+    else
+        sweep_learned_kernel<2><<<ntiles, dim3(Shape<2>::TP, Shape<2>::TA), learned_smem_bytes<2>(), s>>>(
+            a, mlp, kappa, pjump);
+    return cudaGetLastError();
+}
+
+// Host: network parameters (7 x 1379 floats, layout of the public header) to
+// the per-lane B-fragment order the kernel reads.
+void mlp_fragments(const float* params, uint32_t* out) {
+    auto bf = [](float x) -> uint32_t {
+        // round to nearest even bfloat16
+        uint32_t u;
+        memcpy(&u, &x, 4);
+        if ((u & 0x7f800000u) == 0x7f800000u) return u >> 16;
+        const uint32_t r = 0x7fffu + ((u >> 16) & 1u);
+        return (u + r) >> 16;
+    };
+    auto pk = [&](float lo, float hi) { return bf(lo) | (bf(hi) << 16); };
+    auto fbits = [](float x) { uint32_t u; memcpy(&u, &x, 4); return u; };
+    const int NH = 32, NIN = 6;
+    for (int f = 0; f < WB_MLP_NFIELD; f++) {
+        const float* p = params + (size_t)f * WB_MLP_NPARAM;
+        const float* W1 = p;
+        const float* b1 = W1 + NH * NIN;
+        const float* W2 = b1 + NH;
+        const float* b2 = W2 + NH * NH;
+        const float* W3 = b2 + NH;
+        const float* b3 = W3 + 3 * NH;
+        // first layer as 32 x 8: six weights, the bias, a zero
+        auto w1 = [&](int n, int k) { return k < NIN ? W1[n * NIN + k] : (k == NIN ? b1[n] : 0.f); };
+        auto w3 = [&](int n, int k) { return n < 3 ? W3[n * NH + k] : 0.f; };
+        for (int lane = 0; lane < 32; lane++) {
+            const int g = lane >> 2, t = lane & 3;
+            uint32_t* o = out + (size_t)f * kMlpWords * 32 + lane;
+            for (int nt = 0; nt < 4; nt++) o[nt * 32] = pk(w1(8 * nt + g, 2 * t), w1(8 * nt + g, 2 * t + 1));
+            for (int nt = 0; nt < 4; nt++)
+                for (int kt = 0; kt < 2; kt++) {
+                    const int n = 8 * nt + g, k0 = 16 * kt + 2 * t;
+                    o[(4 + nt * 4 + kt * 2) * 32] = pk(W2[n * NH + k0], W2[n * NH + k0 + 1]);
+                    o[(5 + nt * 4 + kt * 2) * 32] = pk(W2[n * NH + k0 + 8], W2[n * NH + k0 + 9]);
+                }
+            for (int kt = 0; kt < 2; kt++) {
+                const int k0 = 16 * kt + 2 * t;
+                o[(20 + kt * 2) * 32] = pk(w3(g, k0), w3(g, k0 + 1));
+                o[(21 + kt * 2) * 32] = pk(w3(g, k0 + 8), w3(g, k0 + 9));
+            }
+            for (int nt = 0; nt < 4; nt++) {
+                o[(24 + 2 * nt) * 32] = fbits(b2[8 * nt + 2 * t]);
+                o[(25 + 2 * nt) * 32] = fbits(b2[8 * nt + 2 * t + 1]);
+            }
+            o[32 * 32] = fbits(2 * t < 3 ? b3[2 * t] : 0.f);
+            o[33 * 32] = fbits(2 * t + 1 < 3 ? b3[2 * t + 1] : 0.f);
+        }
+    }
+}
+
+size_t mlp_fragment_words() { return (size_t)kMlpSmemWords; }
+
+}  // namespace wb

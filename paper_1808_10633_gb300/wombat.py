@@ -17,16 +17,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwombat_gb300.so")
 
 WB_OK, WB_EINVAL, WB_ECUDA, WB_ENOMEM, WB_ENONFINITE, WB_ETIMEOUT, WB_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
-WB_FP64, WB_FP32 = 0, 1
+WB_FP64, WB_FP32, WB_FP32_LEARNED = 0, 1, 2
 WB_SSPRK3, WB_RK4 = 0, 1
-PRECISIONS = {"fp64": WB_FP64, "fp32": WB_FP32}
+PRECISIONS = {"fp64": WB_FP64, "fp32": WB_FP32, "learned": WB_FP32_LEARNED}
 INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 
 # every entry point declared in include/wombat_gb300.h
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest")
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
     L.wb_alu_peak.argtypes = [i, dp]
     L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
+    L.wb_set_mlp.argtypes = [vp, vp, d, d]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
@@ -203,6 +204,11 @@ class Grid:
         out = np.empty(7 * self.ncells)
         _check(self._lib.wb_face_fluxes(self._h, int(axis), out.ctypes.data))
         return out.reshape(7, self.ncells)
+
+    def set_mlp(self, params, kappa: float = 4.0, pjump: float = 0.5):
+        """Install the learned-weight networks (7 x 1379 floats)."""
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_NFIELD * MLP_NPARAM)
+        _check(self._lib.wb_set_mlp(self._h, p.ctypes.data, float(kappa), float(pjump)))
 
     def harvest(self, axis: int, cells, hU, hF, kappa: float = 4.0, pjump: float = 0.5):
         """Training records (n, 14, 12) for the lower faces of `cells` along axis."""

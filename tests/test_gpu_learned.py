@@ -138,3 +138,147 @@ def test_training_lowers_the_loss(wb):
     loss1, _ = wb.mlp_loss_grad(rec, p, 1e-3)
     assert np.all(np.isfinite(hist))
     assert loss1.mean() < 0.9 * loss0.mean(), (loss0, loss1)
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _sample_learned_fluxes(orc, wb, st, params, kappa, pjump, nsamp, seed, bf16_params=True):
+    from oracle import learned as Lr
+
+    g = wb.Grid.from_state(st, precision="learned")
+    g.set_mlp(params, kappa, pjump)
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = st.dims
+    P = _bf16(params) if bf16_params else np.asarray(params, np.float64)
+    # the first layer's bias and the output bias stay FP32 on the GPU
+    P = P.reshape(7, Lr.NPARAM).copy()
+    p64 = np.asarray(params, np.float64).reshape(7, Lr.NPARAM)
+    o = 32 * 6
+    P[:, o:o + 32] = _bf16(p64[:, o:o + 32])          # b1 enters as a bf16 weight
+    o2 = o + 32 + 32 * 32
+    P[:, o2:o2 + 32] = p64[:, o2:o2 + 32]              # b2 fp32
+    P[:, -3:] = p64[:, -3:]                            # b3 fp32
+    got, ref = [], []
+    for axis in range(3):
+        F = g.face_fluxes(axis)
+        idx = rng.integers(0, [nx, ny, nz], size=(nsamp, 3))
+        n_, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
+        perm = [0, 1 + n_, 1 + t1, 1 + t2, 4 + n_, 4 + t1, 4 + t2, 7]
+        for (i, j, k) in idx:
+            Us = np.empty((6, 8))
+            for m in range(6):
+                q = [i, j, k]
+                q[axis] = (q[axis] + m - 3) % (nx, ny, nz)[axis]
+                Us[m] = st.U[perm, q[2], q[1], q[0]]
+            Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump)
+            r = np.empty(7)
+            r[0] = Fh[0]
+            for gq in range(3):
+                r[1 + gq] = Fh[perm.index(1 + gq)]
+            r[4], r[5], r[6] = Fh[7], Fh[5], Fh[6]
+            c = (k * ny + j) * nx + i
+            got.append(F[:, c])
+            ref.append(r)
+    g.close()
+    return np.array(got), np.array(ref)
+
+
+def test_learned_sweep_linear_network_matches_oracle(orc, wb):
+    from oracle import learned as Lr
+
+    st = I.turbulence(24, seed=31)
+    params = np.tile(Lr.linear_params(), (7, 1)).astype(np.float32)
+    got, ref = _sample_learned_fluxes(orc, wb, st, params, 1e30, 1e30, 40, 1, bf16_params=False)
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-3 * np.abs(ref).max())
+    assert (np.abs(got - ref) / scale).max() < 2e-5
+
+
+def test_learned_sweep_random_network_matches_oracle(orc, wb):
+    """A network far from the linear weights (random, O(1) logits): the
+    tensor-core evaluation (BF16 inputs and weights, FP32 accumulation,
+    hardware tanh) agrees with the FP64 reference on BF16-rounded weights to
+    a few 1e-3 of each flux component's scale, while differing from the
+    Jiang-Shu flux by much more."""
+    rng = np.random.default_rng(12)
+    from oracle import learned as Lr
+
+    params = (rng.standard_normal((7, Lr.NPARAM)) * 0.5).astype(np.float32)
+    st = I.turbulence(24, seed=32)
+    got, ref = _sample_learned_fluxes(orc, wb, st, params, 1e30, 1e30, 40, 2)
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-3 * np.abs(ref).max())
+    err = (np.abs(got - ref) / scale).max()
+    assert err < 5e-3, err
+    # the same faces with Jiang-Shu weights differ by much more
+    g = wb.Grid.from_state(st, precision="fp32")
+    js = np.concatenate([g.face_fluxes(a)[:, :1] for a in range(3)], axis=1)
+    g.close()
+    lg = wb.Grid.from_state(st, precision="learned")
+    lg.set_mlp(params, 1e30, 1e30)
+    ln = np.concatenate([lg.face_fluxes(a)[:, :1] for a in range(3)], axis=1)
+    lg.close()
+    assert np.abs(ln - js).max() / np.abs(js).max() > 10 * err
+
+
+def test_learned_sweep_detector_falls_back_to_js(wb):
+    """With every detector firing (kappa, pjump tiny) the learned sweep gives
+    the Jiang-Shu fluxes."""
+    rng = np.random.default_rng(13)
+    params = (rng.standard_normal((7, 1379)) * 0.5).astype(np.float32)
+    st = I.turbulence(24, seed=33)
+    g = wb.Grid.from_state(st, precision="fp32")
+    lg = wb.Grid.from_state(st, precision="learned")
+    lg.set_mlp(params, 1e-30, 1e-30)
+    for a in range(3):
+        F1, F2 = g.face_fluxes(a), lg.face_fluxes(a)
+        assert np.abs(F1 - F2).max() <= 1e-6 * np.abs(F1).max()
+    g.close()
+    lg.close()
+
+
+@pytest.fixture(scope="module")
+def trained(wb):
+    from paper_1808_10633_gb300 import learned as Ln
+
+    st = I.turbulence(64, seed=1808)
+    rec = Ln.harvest(st, 20000, seed=5)
+    p, hist = Ln.train(rec, steps=1500, batch=4096, lr=2e-3, lam=1e-3, seed=6)
+    return p
+
+
+def test_learned_gain_on_alfven_wave(orc, wb, trained):
+    """The trained weights recover accuracy where the Jiang-Shu weights lose
+    it (Sec. 2.1: third order near critical points): on the circularly
+    polarised Alfven wave the L1 error against the exact solution is lower
+    than with the Jiang-Shu weights at the same resolution."""
+    errs = {}
+    for mode in ("fp32", "learned"):
+        e = []
+        for N in (16, 32):
+            st = I.alfven_wave(N, 1, 1, amp=0.1)
+            g = wb.Grid.from_state(st, precision=mode)
+            if mode == "learned":
+                g.set_mlp(trained, 4.0, 0.5)
+            T, n = 0.2, int(np.ceil(0.2 / (0.4 / (3 * 1.2 * N))))
+            g.step(T / n, n)
+            U = g.get_state_single()[0]
+            g.close()
+            ex = I.alfven_wave(N, 1, 1, amp=0.1, t=T)
+            e.append(np.abs(U[5] - ex.U[5]).mean())
+        errs[mode] = e
+    assert errs["learned"][-1] < errs["fp32"][-1], errs
+
+
+def test_learned_blasts_stay_positive(wb, trained):
+    st = I.add_blasts(I.turbulence(48, seed=7), nblast=8)
+    g = wb.Grid.from_state(st, precision="learned")
+    g.set_mlp(trained, 4.0, 0.5)
+    g.step_cfl(0.4, 10)
+    dt = g.cfl_dt(0.4)                  # raises on NaN or rho, p <= 0
+    U = g.get_state_single()[0]
+    g.close()
+    assert dt > 0 and np.isfinite(U).all() and U[0].min() > 0
