@@ -222,6 +222,16 @@ def run_native(args, rank, world, local):
     if g64 is not None:
         g64.close()
 
+    # ---- batched uneven patches (config 4) --------------------------------
+    patches = None
+    if args.patches > 0:
+        patches = run_patches(args, world)
+
+    # ---- learned weights on turbulence + blasts (config 5) -----------------
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(args, st, world, peak32)
+
     # ---- end to end through the ABI with pinned host buffers --------------
     e2e = None
     if not args.no_e2e:
@@ -272,8 +282,121 @@ def run_native(args, rank, world, local):
         "alu_peak_tflops": {"fp32": peak32, "fp64": peak64},
         "clocks": clk,
         "e2e": e2e,
+        "learned": learned,
+        "patches": patches,
     })
     return out
+
+
+def run_patches(args, world):
+    """Independent periodic patches, edges log-uniform in [16, 64] (aspect
+    <= 2), each a rotated Brio-Wu tube or a turbulence state; FP32, one
+    persistent launch per sweep axis with per-patch tile shapes, autotuned."""
+    import torch
+
+    from paper_1808_10633_gb300 import inputs, wombat
+
+    t0 = time.perf_counter()
+    sts = inputs.patch_batch(args.patches, seed=1808)
+    t_gen = time.perf_counter() - t0
+    cells = sum(s.U[0].size for s in sts)
+    g = wombat.Grid.from_patches(sts, precision="fp32")
+    for _ in range(args.warmup):
+        g.step_cfl(args.cfl, 1)
+    g.sync()
+    tot0, kms0, _ = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    tune = g.autotune()
+    for _ in range(2):
+        g.step_cfl(args.cfl, 1)
+    g.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    tot, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    barrier(world)
+    secs = max_over_ranks(tot / 1e3, world)
+    g.sync()
+    t1 = time.perf_counter()
+    g.step_cfl(args.cfl, args.steps)       # CUDA-graph replay
+    g.sync()
+    graph_ms = (time.perf_counter() - t1) * 1e3 / args.steps
+    g.close()
+    return {"workload": f"{args.patches} periodic patches, edges log-uniform in [16,64], "
+                        "Brio-Wu or turbulence, FP32", "cells": int(cells),
+            "value": world * cells * args.steps / secs, "unit": UNIT,
+            "ms_per_step": secs * 1e3 / args.steps, "graph_replay_ms_per_step": graph_ms,
+            "ms_per_step_cost_model_tiles": tot0 / args.steps,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
+                            "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]},
+            "generate_s": t_gen}
+
+
+def _l1(U, ref):
+    names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E"]
+    U = U.reshape(8, -1)
+    ref = ref.reshape(8, -1)
+    return {nm: float(np.abs(U[f] - ref[f]).mean() / max(np.abs(ref[f]).mean(), 1e-300))
+            for f, nm in enumerate(names)}
+
+
+def run_learned(args, st, world, peak32):
+    """Learned weights (BF16 tensor-core MLP per characteristic field, Jiang-
+    Shu where the detectors fire) on the turbulence field with 64 blast
+    spheres.  The networks are trained here, by the library's own harvest,
+    forward/backward and Adam kernels, on faces of a 64^3 turbulence state."""
+    import torch
+
+    from paper_1808_10633_gb300 import inputs, learned as Ln, wombat
+
+    t0 = time.perf_counter()
+    rec = Ln.harvest(inputs.turbulence(64, seed=1808), 20000, seed=5)
+    t_h = time.perf_counter() - t0
+    params, hist = Ln.train(rec, steps=1500, batch=4096, lr=2e-3, lam=1e-3, seed=6)
+    t_t = time.perf_counter() - t0 - t_h
+    st5 = inputs.add_blasts(st, seed=1808, nblast=64)
+    n = args.size
+    zones = n ** 3
+    gl = wombat.Grid.from_state(st5, precision="learned")
+    gl.set_mlp(params, 4.0, 0.5)
+    for _ in range(args.warmup):
+        gl.step_cfl(args.cfl, 1)
+    gl.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    tot, kms, kcnt = gl.step_profiled(args.cfl, args.steps, with_totals=True)
+    barrier(world)
+    secs = max_over_ranks(tot / 1e3, world)
+    value = world * zones * args.steps / secs
+    # MLP work: 14 evaluations (7 fields x 2 sides) of 2*(6*32+32*32+32*3) flops per interface
+    mlp_flops = 14 * 2 * (6 * 32 + 32 * 32 + 32 * 3) * zones
+    cls = max(("sweep_x", "sweep_y", "sweep_z"), key=lambda k: kms[k])
+    ms_l = kms[cls] / max(kcnt[cls], 1)
+    res = {"workload": f"turbulence {n}^3 + 64 blast spheres (p x100, r 0.02-0.05), learned weights",
+           "value": value, "unit": UNIT, "ms_per_step": secs * 1e3 / args.steps,
+           "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "train": {"records": int(rec.shape[0]), "unflagged": int((rec[:, 11] == 0).sum()),
+                     "steps": 1500, "harvest_s": t_h, "train_s": t_t,
+                     "loss_first": float(hist[:20].mean()), "loss_last": float(hist[-20:].mean())},
+           "sweep_mlp_tflops": mlp_flops / (ms_l * 1e-3) / 1e12}
+    if args.l1_steps > 0:
+        nst = max(1, args.l1_steps // 2)
+        b5 = np.stack([st5.bx, st5.by, st5.bz])
+        g64 = wombat.Grid.from_state(st5, precision="fp64")
+        dt = g64.cfl_dt(args.cfl)
+        g64.step(dt, nst)
+        U64, _ = g64.get_state()
+        g64.close()
+        g32 = wombat.Grid.from_state(st5, precision="fp32")
+        g32.step(dt, nst)
+        U32, _ = g32.get_state()
+        g32.close()
+        gl.set_state(st5.U, b5)
+        gl.step(dt, nst)
+        Ul, _ = gl.get_state()
+        res["error_vs_fp64_after_steps"] = nst
+        res["l1_rel_vs_fp64"] = {"learned": _l1(Ul, U64), "fp32_js": _l1(U32, U64)}
+    gl.close()
+    return res
 
 
 def oracle_sample(seconds: float, n: int, cfl: float):
@@ -341,6 +464,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-weights leg")
+    ap.add_argument("--patches", type=int, default=512,
+                    help="patch count of the batched-patch leg (0: skip)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
@@ -348,7 +474,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.fp32_only:
-        args.no_e2e = args.no_cpu = True
+        args.no_e2e = args.no_cpu = args.no_learned = True
+        args.patches = 0
         args.l1_steps = 0
     rank, world, local = dist_env()
     # one GPU per rank: restrict this process to its GPU before CUDA starts,

@@ -78,6 +78,9 @@ typedef struct {
                              sum of the 4 cell values of -v x B (reduces to
                              the 1-D upwind flux for grid-aligned flow);
                              1: plain mean of the 4 face EMFs               */
+    int weights;          /* 0: Jiang-Shu nonlinear weights (Sec. 2.1);
+                             1: WENO-Z weights (the alternative Sec. 2.1
+                             names); not with WB_FP32_LEARNED              */
 } wb_grid_desc;
 
 typedef struct {
@@ -96,7 +99,8 @@ typedef struct {
  * cudaStream_t to order all work on, or NULL for a stream the library
  * creates.  out: receives the grid.  Synchronises.
  * Errors: WB_EINVAL for a null pointer, npatch < 1, a size out of range,
- * ghost != 3, an unknown mode or non-positive dx/dy/dz or gamma <= 1;
+ * ghost != 3, an unknown mode, WENO-Z with learned weights, or
+ * non-positive dx/dy/dz or gamma <= 1;
  * WB_ENOMEM; WB_ECUDA. */
 int wb_init_grid(const wb_grid_desc *d, const double *U0, const double *b0,
                  void *cuda_stream, wb_grid **out);
@@ -142,6 +146,19 @@ int wb_sync(wb_grid *g);
  * mz, E, B_t1, B_t2) with (t1, t2) = (y, z), (z, x), (x, y) for axis 0, 1,
  * 2.  Does not change the state.  Synchronises. */
 int wb_face_fluxes(wb_grid *g, int axis, double *F_out);
+
+/* Autotuner of the sweep tiles.  A sweep tile is TA interfaces along the
+ * axis times 256/TA pencils; each axis has WB_NTILE_SHAPE shapes (default
+ * first).  At wb_init_grid every patch gets the shape that needs the fewest
+ * thread slots for its sizes (a cost model: ragged tiles at patch edges idle
+ * threads).  wb_autotune measures, for each axis, one sweep of the current
+ * state with the cost-model tiles and with each fixed shape (CUDA events,
+ * second of two launches), and keeps the fastest table.  ms_out (host,
+ * 3 * (WB_NTILE_SHAPE + 1), may be NULL): the times, per axis [model,
+ * shape 0, shape 1, shape 2].  Not for WB_FP32_LEARNED grids.
+ * Synchronises. */
+#define WB_NTILE_SHAPE 3
+int wb_autotune(wb_grid *g, double *ms_out);
 
 /* Kernel classes timed by wb_step_profiled. */
 enum {

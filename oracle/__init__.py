@@ -27,7 +27,7 @@ class OrcGrid(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
-        ("gamma", ctypes.c_double), ("emf_mode", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("emf_mode", ctypes.c_int), ("weights", ctypes.c_int),
     ]
 
 
@@ -40,6 +40,9 @@ def lib():
         G = ctypes.POINTER(OrcGrid)
         L.orc_phi_n.restype = d
         L.orc_phi_n.argtypes = [d, d, d, d]
+        L.orc_phi_n_z.restype = d
+        L.orc_phi_n_z.argtypes = [d, d, d, d]
+        L.orc_weno_weights_z.argtypes = [d, d, d, d, _dp, _dp, _dp]
         L.orc_weno_weights.argtypes = [d, d, d, d, _dp, _dp, _dp]
         L.orc_cons_to_prim.argtypes = [_dp, d, _dp]
         L.orc_prim_to_cons.argtypes = [_dp, d, _dp]
@@ -77,6 +80,16 @@ def _vec(x, n):
 # ---------------------------------------------------------------- point-wise
 def phi_n(a, b, c, d) -> float:
     return lib().orc_phi_n(float(a), float(b), float(c), float(d))
+
+
+def phi_n_z(a, b, c, d) -> float:
+    return lib().orc_phi_n_z(float(a), float(b), float(c), float(d))
+
+
+def weno_weights_z(a, b, c, d):
+    w = [ctypes.c_double() for _ in range(3)]
+    lib().orc_weno_weights_z(float(a), float(b), float(c), float(d), *[ctypes.byref(x) for x in w])
+    return tuple(x.value for x in w)
 
 
 def weno_weights(a, b, c, d):
@@ -143,10 +156,11 @@ class Grid:
     dz: float
     gamma: float = 5.0 / 3.0
     emf_mode: int = 0
+    weights: int = 0
 
     def c(self) -> OrcGrid:
         return OrcGrid(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz,
-                       self.gamma, self.emf_mode)
+                       self.gamma, self.emf_mode, self.weights)
 
     @property
     def shape(self):

@@ -58,6 +58,34 @@ void orc_weno_weights(double a, double b, double c, double d,
     *w2 = a2 / s;
 }
 
+/* WENO-Z weights (the fifth-order-everywhere alternative Sec. 2.1 names,
+ * Borges et al. 2008): the same smoothness indicators IS_k and linear
+ * weights 1:6:3, tau5 = |IS_0 - IS_2|,
+ * alpha_k = d_k (1 + tau5 / (eps + IS_k)), omega_k = alpha_k / sum(alpha). */
+void orc_weno_weights_z(double a, double b, double c, double d,
+                        double *w0, double *w1, double *w2)
+{
+    const double eps = 1e-6;
+    double is0 = 13.0 * (a - b) * (a - b) + 3.0 * (a - 3.0 * b) * (a - 3.0 * b);
+    double is1 = 13.0 * (b - c) * (b - c) + 3.0 * (b + c) * (b + c);
+    double is2 = 13.0 * (c - d) * (c - d) + 3.0 * (3.0 * c - d) * (3.0 * c - d);
+    double tau = fabs(is0 - is2);
+    double a0 = 1.0 * (1.0 + tau / (eps + is0));
+    double a1 = 6.0 * (1.0 + tau / (eps + is1));
+    double a2 = 3.0 * (1.0 + tau / (eps + is2));
+    double s = a0 + a1 + a2;
+    *w0 = a0 / s;
+    *w1 = a1 / s;
+    *w2 = a2 / s;
+}
+
+double orc_phi_n_z(double a, double b, double c, double d)
+{
+    double w0, w1, w2;
+    orc_weno_weights_z(a, b, c, d, &w0, &w1, &w2);
+    return w0 * (a - 2.0 * b + c) / 3.0 + (w2 - 0.5) * (b - 2.0 * c + d) / 6.0;
+}
+
 /* Sec. 2.1, WENO5 interpolant
  * phi_N(a,b,c,d) = 1/3 w0 (a - 2b + c) + 1/6 (w2 - 1/2) (b - 2c + d). */
 double orc_phi_n(double a, double b, double c, double d)
@@ -318,6 +346,12 @@ static const int SYS[7] = {0, 1, 2, 3, 5, 6, 7};
  * Fhat[4] (normal B) is zero. */
 void orc_interface_flux(const double Us[48], double gamma, double Fhat[8])
 {
+    orc_interface_flux_w(Us, gamma, 0, Fhat);
+}
+
+void orc_interface_flux_w(const double Us[48], double gamma, int weights, double Fhat[8])
+{
+    double (*phi)(double, double, double, double) = weights == 1 ? orc_phi_n_z : orc_phi_n;
     double W[6][8], F[6][8], lk[6][7];
     for (int k = 0; k < 6; k++) {
         orc_cons_to_prim(&Us[k * 8], gamma, W[k]);
@@ -359,8 +393,7 @@ void orc_interface_flux(const double Us[48], double gamma, double Fhat[8])
             dm[j] = gm[j + 1] - gm[j];
         }
         /* dp[0] is Delta_{i-3/2}, ..., dp[4] is Delta_{i+5/2} */
-        corr[s] = -orc_phi_n(dp[0], dp[1], dp[2], dp[3])
-                  + orc_phi_n(dm[4], dm[3], dm[2], dm[1]);
+        corr[s] = -phi(dp[0], dp[1], dp[2], dp[3]) + phi(dm[4], dm[3], dm[2], dm[1]);
     }
     for (int f = 0; f < 7; f++) {
         int q = SYS[f];
@@ -417,7 +450,7 @@ void orc_face_fluxes(const orc_grid *g, const double *U, int axis, double *F)
                     long c = IDX(g, q[0], q[1], q[2]);
                     for (int f = 0; f < 8; f++) Us[m * 8 + f] = U[perm[f] * N + c];
                 }
-                orc_interface_flux(Us, g->gamma, Fh);
+                orc_interface_flux_w(Us, g->gamma, g->weights, Fh);
                 long c = IDX(g, i, j, k);
                 for (int f = 0; f < 8; f++) F[perm[f] * N + c] = Fh[f];
             }

@@ -37,10 +37,15 @@ typedef struct {
     double gamma;
     int emf_mode;   /* 0: 1-D-consistent EMF (twice the face mean minus the
                           cell mean), 1: plain mean of the four face EMFs   */
+    int weights;    /* 0: Jiang-Shu nonlinear weights (Sec. 2.1),
+                       1: WENO-Z weights (the alternative Sec. 2.1 names) */
 } orc_grid;
 
 /* --- point-wise pieces (Sec. 2.1) ---------------------------------------- */
 double orc_phi_n(double a, double b, double c, double d);
+double orc_phi_n_z(double a, double b, double c, double d);
+void   orc_weno_weights_z(double a, double b, double c, double d,
+                          double *w0, double *w1, double *w2);
 void   orc_weno_weights(double a, double b, double c, double d,
                         double *w0, double *w1, double *w2);
 void   orc_cons_to_prim(const double U[8], double gamma, double W[8]);
@@ -51,6 +56,7 @@ void   orc_wave_speeds(const double W[8], double gamma,
 int    orc_eigen(const double W[8], double gamma, double lam[7],
                  double RU[49], double LU[49]);
 void   orc_interface_flux(const double Us[48], double gamma, double Fhat[8]);
+void   orc_interface_flux_w(const double Us[48], double gamma, int weights, double Fhat[8]);
 
 /* --- grid operators ------------------------------------------------------ */
 void   orc_cell_b(const orc_grid *g, const double *bx, const double *by,

@@ -74,7 +74,7 @@ struct wb_grid {
     int npatch = 0;
     long long N = 0;
     double dx = 0, dy = 0, dz = 0, gamma = 0;
-    int precision = 0, integrator = 0, emf_mode = 0;
+    int precision = 0, integrator = 0, emf_mode = 0, weights = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -87,6 +87,8 @@ struct wb_grid {
     void* emf = nullptr;
     uint32_t* d_mlp = nullptr;            // learned weights, fragment order
     double kappa = 4.0, pjump = 0.5;
+    int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
+    int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
     wb::PatchDev* d_patches = nullptr;
     std::vector<wb::PatchDev> h_patches;
     wb::Tile* d_tiles[3] = {nullptr, nullptr, nullptr};
@@ -128,6 +130,8 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.patches = g->d_patches;
             a.ncells = N;
             a.gamma = g->gamma;
+            a.zweights = g->weights;
+            a.uniform_shape0 = g->tile_uniform[axis];
             int rc = prof_begin(pf, g->stream);
             if (rc != WB_OK) return rc;
             if constexpr (sizeof(T) == 4) {
@@ -291,6 +295,54 @@ void release(wb_grid* g) {
     delete g;
 }
 
+// Sweep tiles of `axis` for every patch.  policy >= 0: that tile shape
+// everywhere; policy < 0: per patch the shape needing the fewest thread slots
+// (ragged tiles at the patch edges idle threads), ties to the lower shape.
+// The shape goes into the top byte of the tile's patch field.
+std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
+    std::vector<wb::Tile> out;
+    for (int p = 0; p < g->npatch; p++) {
+        const wb::PatchDev& P = g->h_patches[p];
+        const int na = axis == 0 ? P.nx : (axis == 1 ? P.ny : P.nz);
+        const int npn = axis == 0 ? P.ny : P.nx;
+        const int n3 = axis == 0 ? P.nz : (axis == 1 ? P.nz : P.ny);
+        int best = policy;
+        if (policy < 0) {
+            long long slots = -1;
+            for (int sh = 0; sh < wb::kNTileShape; sh++) {
+                int ta, tp;
+                wb::sweep_shape(axis, sh, &ta, &tp);
+                const long long n = (long long)((na + ta - 1) / ta) * ((npn + tp - 1) / tp) * n3;
+                if (slots < 0 || n < slots) { slots = n; best = sh; }
+            }
+        }
+        int ta, tp;
+        wb::sweep_shape(axis, best, &ta, &tp);
+        const int px = p | (best << 24);
+        if (axis == 0) {
+            for (int z = 0; z < P.nz; z++)
+                for (int y0 = 0; y0 < P.ny; y0 += tp)
+                    for (int x0 = 0; x0 < P.nx; x0 += ta) out.push_back(wb::Tile{px, x0, y0, z});
+        } else if (axis == 1) {
+            for (int z = 0; z < P.nz; z++)
+                for (int y0 = 0; y0 < P.ny; y0 += ta)
+                    for (int x0 = 0; x0 < P.nx; x0 += tp) out.push_back(wb::Tile{px, y0, x0, z});
+        } else {
+            for (int y = 0; y < P.ny; y++)
+                for (int z0 = 0; z0 < P.nz; z0 += ta)
+                    for (int x0 = 0; x0 < P.nx; x0 += tp) out.push_back(wb::Tile{px, z0, x0, y});
+        }
+    }
+    return out;
+}
+
+// 1 when every tile uses shape 0 (then one tile per block, no dispatch).
+int tiles_uniform(const std::vector<wb::Tile>& t) {
+    for (const wb::Tile& x : t)
+        if ((unsigned)x.x >> 24) return 0;
+    return 1;
+}
+
 template <class P>
 int dmalloc(wb_grid* g, P** p, size_t bytes) {
     WB_CK(cudaMalloc(reinterpret_cast<void**>(p), bytes));
@@ -310,6 +362,8 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     a.patches = g->d_patches;
     a.ncells = N;
     a.gamma = g->gamma;
+    a.zweights = g->weights;
+    a.uniform_shape0 = g->tile_uniform[axis];
     if constexpr (sizeof(T) == 4) {
         if (g->precision == WB_FP32_LEARNED) {
             if (!g->d_mlp) return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
@@ -327,6 +381,34 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     WB_CK(cudaMemcpyAsync(F_out, g->d_io, sizeof(double) * 7 * N, cudaMemcpyDeviceToHost,
                           g->stream));
     WB_CK(cudaStreamSynchronize(g->stream));
+    return WB_OK;
+}
+
+template <class T>
+int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, int uniform, float* ms) {
+    wb::SweepArgs<T> a;
+    a.src = static_cast<const T*>(g->un);
+    a.flux = static_cast<T*>(g->flux) + (long long)axis * wb::kNFlux * g->N;
+    a.er = nullptr;
+    a.tiles = tiles;
+    a.patches = g->d_patches;
+    a.ncells = g->N;
+    a.gamma = g->gamma;
+    a.zweights = g->weights;
+    a.uniform_shape0 = uniform;
+    cudaEvent_t e0, e1;
+    WB_CK(cudaEventCreate(&e0));
+    WB_CK(cudaEventCreate(&e1));
+    WB_CK(wb::launch_sweep<T>(axis, a, ntiles, g->stream));
+    WB_CK(cudaEventRecord(e0, g->stream));
+    WB_CK(wb::launch_sweep<T>(axis, a, ntiles, g->stream));
+    WB_CK(wb::launch_sweep<T>(axis, a, ntiles, g->stream));
+    WB_CK(cudaEventRecord(e1, g->stream));
+    WB_CK(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms *= 0.5f;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return WB_OK;
 }
 
@@ -357,12 +439,16 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (d->integrator != WB_SSPRK3 && d->integrator != WB_RK4)
         return fail(WB_EINVAL, "unknown integrator %d", d->integrator);
     if (d->emf_mode != 0 && d->emf_mode != 1) return fail(WB_EINVAL, "unknown emf_mode %d", d->emf_mode);
+    if (d->weights != 0 && d->weights != 1) return fail(WB_EINVAL, "unknown weights %d", d->weights);
+    if (d->weights == 1 && d->precision == WB_FP32_LEARNED)
+        return fail(WB_EINVAL, "WENO-Z weights and learned weights exclude each other");
 
     wb_grid* g = new (std::nothrow) wb_grid();
     if (!g) return fail(WB_ENOMEM, "host allocation failed");
     g->npatch = d->npatch;
     g->dx = d->dx; g->dy = d->dy; g->dz = d->dz; g->gamma = d->gamma;
     g->precision = d->precision; g->integrator = d->integrator; g->emf_mode = d->emf_mode;
+    g->weights = d->weights;
     g->tsize = d->precision == WB_FP64 ? 8 : 4;
     long long off = 0;
     for (int p = 0; p < d->npatch; p++) {
@@ -400,27 +486,16 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     // tiles and cell blocks
     std::vector<wb::Tile> tiles[3];
     std::vector<wb::CellBlock> blocks;
+    for (int a = 0; a < 3; a++) tiles[a] = build_tiles(g, a, g->precision == WB_FP32_LEARNED ? 0 : -1);
     for (int p = 0; p < g->npatch; p++) {
         const wb::PatchDev& P = g->h_patches[p];
-        int ta, tp;
-        wb::sweep_tile_shape(0, &ta, &tp);
-        for (int z = 0; z < P.nz; z++)
-            for (int y0 = 0; y0 < P.ny; y0 += tp)
-                for (int x0 = 0; x0 < P.nx; x0 += ta) tiles[0].push_back(wb::Tile{p, x0, y0, z});
-        wb::sweep_tile_shape(1, &ta, &tp);
-        for (int z = 0; z < P.nz; z++)
-            for (int y0 = 0; y0 < P.ny; y0 += ta)
-                for (int x0 = 0; x0 < P.nx; x0 += tp) tiles[1].push_back(wb::Tile{p, y0, x0, z});
-        wb::sweep_tile_shape(2, &ta, &tp);
-        for (int y = 0; y < P.ny; y++)
-            for (int z0 = 0; z0 < P.nz; z0 += ta)
-                for (int x0 = 0; x0 < P.nx; x0 += tp) tiles[2].push_back(wb::Tile{p, z0, x0, y});
         const long long np = (long long)P.nx * P.ny * P.nz;
         for (long long c = 0; c < np; c += wb::kCellBlock) blocks.push_back(wb::CellBlock{p, (int)c});
     }
     for (int a = 0; a < 3; a++) {
         if (tiles[a].size() > 0x7fffffffULL) return bail(fail(WB_EINVAL, "grid too large"));
         g->ntiles[a] = (int)tiles[a].size();
+        g->tile_uniform[a] = tiles_uniform(tiles[a]);
     }
     g->nblocks = (int)blocks.size();
 
@@ -642,6 +717,51 @@ int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
     g->kappa = kappa;
     g->pjump = pjump;
     if (g->graph) {              // kernel arguments changed: capture again
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    return WB_OK;
+}
+
+int wb_autotune(wb_grid* g, double* ms_out) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (g->precision == WB_FP32_LEARNED) return fail(WB_EINVAL, "autotune: learned grids use the default tiles");
+    WB_CK(cudaSetDevice(g->device));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    for (int axis = 0; axis < 3; axis++) {
+        float best_ms = -1.f;
+        int best = -2;
+        for (int c = 0; c <= wb::kNTileShape; c++) {
+            const int policy = c == 0 ? -1 : c - 1;     // 0: per-patch model, then each fixed shape
+            std::vector<wb::Tile> t = build_tiles(g, axis, policy);
+            wb::Tile* d = nullptr;
+            WB_CK(cudaMalloc(&d, sizeof(wb::Tile) * t.size()));
+            int rc = WB_OK;
+            float ms = 0.f;
+            if (cudaMemcpy(d, t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = fail(WB_ECUDA, "autotune: tile upload failed");
+            const int uni = tiles_uniform(t);
+            if (rc == WB_OK)
+                rc = g->precision == WB_FP64 ? time_sweep<double>(g, axis, d, (int)t.size(), uni, &ms)
+                                             : time_sweep<float>(g, axis, d, (int)t.size(), uni, &ms);
+            cudaFree(d);
+            if (rc != WB_OK) return rc;
+            if (ms_out) ms_out[axis * (wb::kNTileShape + 1) + c] = ms;
+            if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = policy; }
+        }
+        std::vector<wb::Tile> t = build_tiles(g, axis, best);
+        if ((int)t.size() != g->ntiles[axis]) {
+            cudaFree(g->d_tiles[axis]);
+            g->d_tiles[axis] = nullptr;
+            WB_CK(cudaMalloc(&g->d_tiles[axis], sizeof(wb::Tile) * t.size()));
+            g->ntiles[axis] = (int)t.size();
+        }
+        WB_CK(cudaMemcpy(g->d_tiles[axis], t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice));
+        g->tile_policy[axis] = best;
+        g->tile_uniform[axis] = tiles_uniform(t);
+    }
+    if (g->graph) {              // tile tables changed: capture again
         cudaGraphExecDestroy(g->graph);
         g->graph = nullptr;
     }

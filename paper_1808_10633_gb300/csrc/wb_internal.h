@@ -37,6 +37,8 @@ struct SweepArgs {
     const PatchDev* __restrict__ patches;
     long long ncells;              // stride between arrays
     double gamma;
+    int zweights = 0;              // 1: WENO-Z weights instead of Jiang-Shu
+    int uniform_shape0 = 0;        // 1: every tile uses shape 0 (one tile per block)
 };
 
 template <class T>
@@ -66,7 +68,10 @@ template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s);
 template <class T>
 cudaError_t prepare_sweep_kernels();
-void sweep_tile_shape(int axis, int* ta, int* tp);
+// Tile shape s (0 = default, kNTileShape alternatives) of the sweep along
+// `axis`: ta interfaces along the axis times tp pencils (ta * tp = 256).
+constexpr int kNTileShape = 3;
+void sweep_shape(int axis, int s, int* ta, int* tp);
 
 template <class T>
 cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);

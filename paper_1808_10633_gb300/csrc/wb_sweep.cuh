@@ -96,11 +96,30 @@ __device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
     return w0 * (a - 2.0f * b + c) * (1.0f / 3.0f) + (w2 - 0.5f) * (b - 2.0f * c + d) * (1.0f / 6.0f);
 }
 
+// WENO-Z interpolant (the alternative Sec. 2.1 names): same IS_k, weights
+// alpha_k = d_k (1 + tau5 / (eps + IS_k)), tau5 = |IS_0 - IS_2|.
+template <class T>
+__device__ __forceinline__ T phi_n_z(T a, T b, T c, T d) {
+    const T eps = T(1e-6);
+    const T t0 = a - b, t1 = a - T(3) * b;
+    const T is0 = T(13) * t0 * t0 + T(3) * t1 * t1;
+    const T t2 = b - c, t3 = b + c;
+    const T is1 = T(13) * t2 * t2 + T(3) * t3 * t3;
+    const T t4 = c - d, t5 = T(3) * c - d;
+    const T is2 = T(13) * t4 * t4 + T(3) * t5 * t5;
+    const T tau = is0 > is2 ? is0 - is2 : is2 - is0;
+    const T a0 = T(1) + tau / (eps + is0);
+    const T a1 = T(6) * (T(1) + tau / (eps + is1));
+    const T a2 = T(3) * (T(1) + tau / (eps + is2));
+    const T r = T(1) / (a0 + a1 + a2);
+    return a0 * r * (a - T(2) * b + c) * T(1.0 / 3.0) + (a2 * r - T(0.5)) * (b - T(2) * c + d) * T(1.0 / 6.0);
+}
+
 // Correction of eq. FWENO for one characteristic field:
 // -phi_N(D+_{i-3/2}, D+_{i-1/2}, D+_{i+1/2}, D+_{i+3/2})
 // +phi_N(D-_{i+5/2}, D-_{i+3/2}, D-_{i+1/2}, D-_{i-1/2}),
 // D+-_{k+1/2} = g+-_{k+1} - g+-_k, g+- = (g +- alpha w)/2.
-template <class T>
+template <class T, bool Z = false>
 __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha) {
     const T ha = T(0.5) * alpha;
     T gp[5], gm[5];
@@ -111,14 +130,17 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
     // gm[k] holds g-_{k+1}
     T dp0 = gp[1] - gp[0], dp1 = gp[2] - gp[1], dp2 = gp[3] - gp[2], dp3 = gp[4] - gp[3];
     T dm1 = gm[1] - gm[0], dm2 = gm[2] - gm[1], dm3 = gm[3] - gm[2], dm4 = gm[4] - gm[3];
+    if constexpr (Z) return phi_n_z(dm4, dm3, dm2, dm1) - phi_n_z(dp0, dp1, dp2, dp3);
     return phi_n(dm4, dm3, dm2, dm1) - phi_n(dp0, dp1, dp2, dp3);
 }
 
-// Weight policy of the classic scheme: Jiang-Shu weights for every field.
+// Weight policy of the classic scheme: Jiang-Shu weights for every field,
+// or the WENO-Z weights when z is set (uniform over the launch).
 template <class T>
 struct JsWeights {
+    bool z;
     __device__ __forceinline__ T corr(int, const T (&w)[6], const T (&g)[6], T alpha) {
-        return weno_corr<T>(w, g, alpha);
+        return z ? weno_corr<T, true>(w, g, alpha) : weno_corr<T>(w, g, alpha);
     }
 };
 
@@ -582,29 +604,42 @@ template <> struct Shape<2> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256
 template <class T> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB_F32; };
 
-template <class T, int AXIS>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A) {
-    constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
+// Tile shapes a tile may use, per axis: TA interfaces along the axis times
+// TP = 256 / TA pencils.  Shape 0 is the default; the host picks a shape per
+// patch (fewest thread slots for the patch's sizes) and stores it in the top
+// byte of the tile's patch field.
+__host__ __device__ constexpr int shape_ta(int axis, int s) {
+    return axis == 0 ? (s == 0 ? WB_SWEEP_TA_X : (s == 1 ? 64 : 16))
+                     : (s == 0 ? WB_SWEEP_TA_YZ : (s == 1 ? 8 : 32));
+}
+constexpr int kNShape = 3;
+__host__ __device__ constexpr int nc_of(int ta) { return (ta + 5) * (256 / ta); }
+__host__ __device__ constexpr int max_nc(int axis) {
+    return nc_of(shape_ta(axis, 0)) > nc_of(shape_ta(axis, 1))
+               ? (nc_of(shape_ta(axis, 0)) > nc_of(shape_ta(axis, 2)) ? nc_of(shape_ta(axis, 0)) : nc_of(shape_ta(axis, 2)))
+               : (nc_of(shape_ta(axis, 1)) > nc_of(shape_ta(axis, 2)) ? nc_of(shape_ta(axis, 1)) : nc_of(shape_ta(axis, 2)));
+}
+
+// One tile: stage the TA+5 cells of each of the TP pencils, then one thread
+// per interface.
+template <class T, int AXIS, int TA, int NCMAX>
+__device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& tile, const PatchDev& P,
+                                          T* __restrict__ sm, int tid) {
+    constexpr int TP = 256 / TA;
     constexpr int NS = TA + 5;
     constexpr int NC = NS * TP;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
-
-    const Tile tile = A.tiles[blockIdx.x];
-    const PatchDev P = A.patches[tile.x];
     const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
     const int np = AXIS == 0 ? P.ny : P.nx;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
 
     // staging: cells tile.y-3 .. tile.y+TA+1 along the axis, TP pencils
-    constexpr int NIT = (NC + TA * TP - 1) / (TA * TP);
+    constexpr int NIT = (NC + 255) / 256;
     RawCell<T> raw[NIT];
     long long rc[NIT];
     int ridx[NIT];
     bool rok[NIT], rown[NIT];
 #pragma unroll
     for (int it = 0; it < NIT; it++) {
-        const int e = tid + it * TA * TP;
+        const int e = tid + it * 256;
         int s, tp;
         if (AXIS == 0) { tp = e / NS; s = e - tp * NS; }
         else { s = e / TP; tp = e - s * TP; }
@@ -627,17 +662,18 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         if (rok[it]) derive_cell<T, AXIS>(A, raw[it], rc[it], sm, NC, ridx[it], rown[it] && A.er != nullptr);
     __syncthreads();
 
-    const int ta = AXIS == 0 ? threadIdx.x : threadIdx.y;
-    const int tp = AXIS == 0 ? threadIdx.y : threadIdx.x;
+    int ta, tp;
+    if (AXIS == 0) { ta = tid % TA; tp = tid / TA; }
+    else { tp = tid % TP; ta = tid / TP; }
     const int ia = tile.y + ta, ip = tile.z + tp;
     if (ia >= na || ip >= np) return;
     int id[6];
 #pragma unroll
     for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
     T F[7];
-    T* bp = sm + kNSlot * NC + tid;      // this thread's back-projection slots
-    JsWeights<T> js;
-    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, js, F);
+    T* bp = sm + kNSlot * NCMAX + tid;      // this thread's back-projection slots
+    JsWeights<T> js{A.zweights != 0};
+    interface_flux<T>(sm, NC, id, T(A.gamma), bp, 256, js, F);
 
     // rotate back and store at the lower face of cell ia
     int i, j, k;
@@ -660,33 +696,120 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     fo[6 * N + c] = F[5];
 }
 
+// Persistent sweep: a grid of (SMs x resident blocks) strides over the tile
+// table; each tile is dispatched to the body of its shape (a block-uniform
+// branch), so patches of uneven sizes share one launch.
+template <class T, int AXIS>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
+    constexpr int NCMAX = max_nc(AXIS);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        Tile tile = A.tiles[t];
+        const int shape = (unsigned)tile.x >> 24;
+        tile.x &= 0xffffff;
+        const PatchDev P = A.patches[tile.x];
+        if (shape == 0) tile_body<T, AXIS, shape_ta(AXIS, 0), NCMAX>(A, tile, P, sm, tid);
+        else if (shape == 1) tile_body<T, AXIS, shape_ta(AXIS, 1), NCMAX>(A, tile, P, sm, tid);
+        else tile_body<T, AXIS, shape_ta(AXIS, 2), NCMAX>(A, tile, P, sm, tid);
+        __syncthreads();
+    }
+}
+
+// One tile per block, default shape: the launch for tile tables that use
+// shape 0 throughout (a single grid, or patches tuned to it).
+template <class T, int AXIS>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel_fixed(const SweepArgs<T> A) {
+    constexpr int NC0 = nc_of(shape_ta(AXIS, 0));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    Tile tile = A.tiles[blockIdx.x];
+    tile.x &= 0xffffff;
+    const PatchDev P = A.patches[tile.x];
+    tile_body<T, AXIS, shape_ta(AXIS, 0), NC0>(A, tile, P, sm, threadIdx.x);
+}
+
+template <class T, int AXIS>
+constexpr size_t smem_bytes_fixed() {
+    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNBack * 256);
+}
+
 template <class T, int AXIS>
 constexpr size_t smem_bytes() {
     return sizeof(T) * (kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP
                         + kNBack * Shape<AXIS>::TA * Shape<AXIS>::TP);
 }
 
+template <class T, int AXIS>
+constexpr size_t smem_bytes_persistent() {
+    return sizeof(T) * (kNSlot * max_nc(AXIS) + kNBack * 256);
+}
+
 }  // namespace
+
+// Persistent grid sizes per axis, set by prepare_sweep_kernels (outside any
+// stream capture).
+template <class T>
+struct PersistGrid {
+    static inline int g[3] = {0, 0, 0};
+};
+
+// Resident blocks per SM of the persistent sweep of `axis` (for the grid size).
+template <class T>
+int sweep_blocks_per_sm(int axis) {
+    int nb = 0;
+    if (axis == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 0>, 256, smem_bytes_persistent<T, 0>());
+    else if (axis == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 1>, 256, smem_bytes_persistent<T, 1>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 2>, 256, smem_bytes_persistent<T, 2>());
+    return nb > 0 ? nb : 1;
+}
 
 template <class T>
 cudaError_t prepare_sweep_kernels() {
     cudaError_t e;
     e = cudaFuncSetAttribute(sweep_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<T, 0>());
+                             (int)smem_bytes_persistent<T, 0>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sweep_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<T, 1>());
+                             (int)smem_bytes_persistent<T, 1>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<T, 2>());
+    e = cudaFuncSetAttribute(sweep_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_persistent<T, 2>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_fixed<T, 0>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_fixed<T, 1>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_fixed<T, 2>());
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    for (int a = 0; a < 3; a++) PersistGrid<T>::g[a] = nsm * sweep_blocks_per_sm<T>(a);
+    return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (axis == 0) sweep_kernel<T, 0><<<ntiles, dim3(Shape<0>::TA, Shape<0>::TP), smem_bytes<T, 0>(), s>>>(a);
-    else if (axis == 1) sweep_kernel<T, 1><<<ntiles, dim3(Shape<1>::TP, Shape<1>::TA), smem_bytes<T, 1>(), s>>>(a);
-    else sweep_kernel<T, 2><<<ntiles, dim3(Shape<2>::TP, Shape<2>::TA), smem_bytes<T, 2>(), s>>>(a);
+    if (a.uniform_shape0) {
+        if (axis == 0) sweep_kernel_fixed<T, 0><<<ntiles, 256, smem_bytes_fixed<T, 0>(), s>>>(a);
+        else if (axis == 1) sweep_kernel_fixed<T, 1><<<ntiles, 256, smem_bytes_fixed<T, 1>(), s>>>(a);
+        else sweep_kernel_fixed<T, 2><<<ntiles, 256, smem_bytes_fixed<T, 2>(), s>>>(a);
+        return cudaGetLastError();
+    }
+    const int grid = PersistGrid<T>::g[axis] > 0 ? PersistGrid<T>::g[axis] : 152;
+    const int nb = ntiles < grid ? ntiles : grid;
+    if (axis == 0) sweep_kernel<T, 0><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
+    else if (axis == 1) sweep_kernel<T, 1><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
+    else sweep_kernel<T, 2><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
     return cudaGetLastError();
 }
 

@@ -4,10 +4,9 @@
 
 namespace wb {
 
-void sweep_tile_shape(int axis, int* ta, int* tp) {
-    if (axis == 0) { *ta = Shape<0>::TA; *tp = Shape<0>::TP; }
-    else if (axis == 1) { *ta = Shape<1>::TA; *tp = Shape<1>::TP; }
-    else { *ta = Shape<2>::TA; *tp = Shape<2>::TP; }
+void sweep_shape(int axis, int s, int* ta, int* tp) {
+    *ta = shape_ta(axis, s);
+    *tp = 256 / *ta;
 }
 
 template cudaError_t prepare_sweep_kernels<double>();

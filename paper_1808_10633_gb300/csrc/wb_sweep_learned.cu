@@ -15,7 +15,7 @@
 // fragments are re-packed in registers as the next layer's A fragments; the
 // weights sit in shared memory already in B-fragment order (34 words per lane
 // per field, written by wb_set_mlp on the host side).  GELU uses the
-// hardware tanh approximation.  Batch rows are independent, so a lane whose
+// hardware tanh approximation on BF16 pairs.  Batch rows are independent, so a lane whose
 // interface lies outside the patch still joins the warp-wide products (with
 // a valid stencil) and only skips its store.
 #include "wb_sweep.cuh"
@@ -49,11 +49,23 @@ __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], u
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu_fast(float x) {
-    const float u = 0.7978845608f * (x + 0.044715f * x * x * x);
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    return 0.5f * x * (1.0f + t);
+// GELU of two FP32 accumulators, returned as the next layer's BF16 operand
+// pair.  The whole formula runs on the packed pair in BF16 (its result is
+// rounded to BF16 anyway): u = c x (1 + 0.044715 x^2), t = tanh(u),
+// gelu = 0.5 x (1 + t).
+__device__ __forceinline__ uint32_t gelu2(float a, float b) {
+    const uint32_t x = pack_bf16(a, b);
+    const uint32_t c1 = pack_bf16(0.044715f, 0.044715f), one = pack_bf16(1.0f, 1.0f);
+    const uint32_t cg = pack_bf16(0.7978845608f, 0.7978845608f), half = pack_bf16(0.5f, 0.5f);
+    uint32_t x2, p, u, t, h, r;
+    asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(x2) : "r"(x));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(x2), "r"(c1), "r"(one));   // 1 + c1 x^2
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(x), "r"(cg));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(u), "r"(p));                     // c x (1 + c1 x^2)
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(u));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(x), "r"(half));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));                // h + h t
+    return r;
 }
 
 // One warp, one field: omega (w0, w2) for the 64 rows of `in` (row r holds 8
@@ -75,10 +87,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
         uint32_t A2[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A2[kt][0] = pack_bf16(gelu_fast(c1[2 * kt][0]), gelu_fast(c1[2 * kt][1]));
-            A2[kt][1] = pack_bf16(gelu_fast(c1[2 * kt][2]), gelu_fast(c1[2 * kt][3]));
-            A2[kt][2] = pack_bf16(gelu_fast(c1[2 * kt + 1][0]), gelu_fast(c1[2 * kt + 1][1]));
-            A2[kt][3] = pack_bf16(gelu_fast(c1[2 * kt + 1][2]), gelu_fast(c1[2 * kt + 1][3]));
+            A2[kt][0] = gelu2(c1[2 * kt][0], c1[2 * kt][1]);
+            A2[kt][1] = gelu2(c1[2 * kt][2], c1[2 * kt][3]);
+            A2[kt][2] = gelu2(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
+            A2[kt][3] = gelu2(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
         }
         float c2[4][4];
 #pragma unroll
@@ -93,10 +105,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
         uint32_t A3[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A3[kt][0] = pack_bf16(gelu_fast(c2[2 * kt][0]), gelu_fast(c2[2 * kt][1]));
-            A3[kt][1] = pack_bf16(gelu_fast(c2[2 * kt][2]), gelu_fast(c2[2 * kt][3]));
-            A3[kt][2] = pack_bf16(gelu_fast(c2[2 * kt + 1][0]), gelu_fast(c2[2 * kt + 1][1]));
-            A3[kt][3] = pack_bf16(gelu_fast(c2[2 * kt + 1][2]), gelu_fast(c2[2 * kt + 1][3]));
+            A3[kt][0] = gelu2(c2[2 * kt][0], c2[2 * kt][1]);
+            A3[kt][1] = gelu2(c2[2 * kt][2], c2[2 * kt][3]);
+            A3[kt][2] = gelu2(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
+            A3[kt][3] = gelu2(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
         }
         const float b3lo = Wf[32 * 32 + lane], b3hi = Wf[33 * 32 + lane];
         float c3[4] = {b3lo, b3hi, b3lo, b3hi};

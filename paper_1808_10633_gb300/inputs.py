@@ -208,48 +208,54 @@ def brio_wu_patch(dims, rng, bn=0.75, gamma=GAMMA, h=None) -> State:
     """Rotated Brio-Wu tube on a periodic patch.
 
     Left (rho, p, B_t) = (1, 1, 1), right (0.125, 0.1, -1), B_n = bn, at rest.
-    The normal n is a seeded random unit vector; the state follows the sign of
-    sin(2 pi n.x / l) with l the patch's longest edge, so seams may appear at
-    the periodic boundary.  The tangential field comes from the curl of an
-    edge potential (face divergence zero), the normal field is uniform."""
+    The phase phi = 2 pi sum_d m_d x_d / L_d uses a seeded integer vector m
+    (entries in -1..1, not all zero), so the pattern is periodic on the patch
+    and has no seam; the state follows the sign of sin(phi), the normal is
+    grad phi / |grad phi|.  The tangential field is the curl of an edge
+    potential A = (t x n) Phi(phi) with Phi a periodic triangle wave (face
+    divergence zero), the normal field is uniform."""
     nx, ny, nz = dims
     h = h or 1.0 / max(dims)
     shape = (nz, ny, nx)
-    nvec = rng.standard_normal(3)
-    nvec /= np.linalg.norm(nvec)
+    L = np.array([nx, ny, nz], dtype=float) * h
+    while True:
+        m = rng.integers(-1, 2, 3)
+        if np.any(m != 0):
+            break
+    kvec = 2.0 * np.pi * m / L
+    K = np.linalg.norm(kvec)
+    nvec = kvec / K
     tmp = np.array([1.0, 0.0, 0.0]) if abs(nvec[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
     tvec = np.cross(nvec, tmp)
     tvec /= np.linalg.norm(tvec)
     mvec = np.cross(tvec, nvec)
-    ell = max(dims) * h
-    k = 2.0 * np.pi / ell
 
-    def xi(ox, oy, oz):
+    def phase(ox, oy, oz):
         x = (np.arange(nx) + ox) * h
         y = (np.arange(ny) + oy) * h
         z = (np.arange(nz) + oz) * h
         Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
-        return nvec[0] * X + nvec[1] * Y + nvec[2] * Z
+        return kvec[0] * X + kvec[1] * Y + kvec[2] * Z
 
-    def phi(s):
-        # antiderivative of sign(sin(k s)): periodic triangle wave
-        ph = np.mod(k * s, 2.0 * np.pi)
-        return np.where(ph < np.pi, ph / k, (2.0 * np.pi - ph) / k)
+    def Phi(ph):
+        # antiderivative in x of sign(sin phi): d/dphi of K*Phi is sign(sin phi)
+        q = np.mod(ph, 2.0 * np.pi)
+        return np.where(q < np.pi, q, 2.0 * np.pi - q) / K
 
     # edge positions: Ax (i, j-1/2, k-1/2), Ay (i-1/2, j, k-1/2), Az (i-1/2, j-1/2, k)
-    Ax = mvec[0] * phi(xi(0.5, 0.0, 0.0))
-    Ay = mvec[1] * phi(xi(0.0, 0.5, 0.0))
-    Az = mvec[2] * phi(xi(0.0, 0.0, 0.5))
+    Ax = mvec[0] * Phi(phase(0.5, 0.0, 0.0))
+    Ay = mvec[1] * Phi(phase(0.0, 0.5, 0.0))
+    Az = mvec[2] * Phi(phase(0.0, 0.0, 0.5))
     bx, by, bz = curl_faces(Ax, Ay, Az, h, h, h)
     bx = bx + bn * nvec[0]
     by = by + bn * nvec[1]
     bz = bz + bn * nvec[2]
-    left = np.sin(k * xi(0.5, 0.5, 0.5)) >= 0.0
+    left = np.sin(phase(0.5, 0.5, 0.5)) >= 0.0
     rho = np.where(left, 1.0, 0.125)
     p = np.where(left, 1.0, 0.1)
     zero = np.zeros(shape)
     return assemble(rho, zero, zero, zero, p, bx, by, bz, h, h, h, gamma,
-                    {"kind": "brio_wu", "normal": nvec.tolist()})
+                    {"kind": "brio_wu", "normal": nvec.tolist(), "m": m.tolist()})
 
 
 def patch_dims(npatch, seed=1808, lo=16, hi=64, max_aspect=2.0):

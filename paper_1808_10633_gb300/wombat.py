@@ -26,7 +26,7 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp")
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -42,7 +42,7 @@ class GridDesc(ctypes.Structure):
         ("npatch", ctypes.c_int), ("dims", ctypes.POINTER(ctypes.c_int)),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("ghost", ctypes.c_int), ("precision", ctypes.c_int),
-        ("integrator", ctypes.c_int), ("emf_mode", ctypes.c_int),
+        ("integrator", ctypes.c_int), ("emf_mode", ctypes.c_int), ("weights", ctypes.c_int),
     ]
 
 
@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
     L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
     L.wb_set_mlp.argtypes = [vp, vp, d, d]
+    L.wb_autotune.argtypes = [vp, vp]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
@@ -115,7 +116,7 @@ class Grid:
     layout; b: faces (3, nz, ny, nx) or flat.  dims: list of (nx, ny, nz)."""
 
     def __init__(self, dims: Sequence[Sequence[int]], dx, dy, dz, U, b, gamma=5.0 / 3.0,
-                 precision="fp64", integrator="ssprk3", emf_mode=0, stream=None):
+                 precision="fp64", integrator="ssprk3", emf_mode=0, stream=None, weights="js"):
         L = load()
         self._lib = L
         self.dims = [tuple(int(v) for v in d) for d in dims]
@@ -126,7 +127,7 @@ class Grid:
                         float(dx), float(dy), float(dz), float(gamma), 3,
                         PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision,
                         INTEGRATORS.get(integrator, integrator) if isinstance(integrator, str) else integrator,
-                        int(emf_mode))
+                        int(emf_mode), {"js": 0, "z": 1}.get(weights, weights))
         self.precision = precision
         U = self._host(U, 8)
         b = self._host(b, 3)
@@ -204,6 +205,13 @@ class Grid:
         out = np.empty(7 * self.ncells)
         _check(self._lib.wb_face_fluxes(self._h, int(axis), out.ctypes.data))
         return out.reshape(7, self.ncells)
+
+    def autotune(self) -> np.ndarray:
+        """Measure and keep the fastest sweep tile tables; times (3, 4) in ms
+        per axis for [per-patch model, shape 0, shape 1, shape 2]."""
+        ms = np.empty(12)
+        _check(self._lib.wb_autotune(self._h, ms.ctypes.data))
+        return ms.reshape(3, 4)
 
     def set_mlp(self, params, kappa: float = 4.0, pjump: float = 0.5):
         """Install the learned-weight networks (7 x 1379 floats)."""

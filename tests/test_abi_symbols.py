@@ -53,13 +53,14 @@ def test_version_string(lib):
 def _desc(wombat, **over):
     dims = np.array([8, 8, 8], dtype=np.int32)
     kw = dict(npatch=1, dims=dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), dx=0.1, dy=0.1,
-              dz=0.1, gamma=5 / 3, ghost=3, precision=0, integrator=0, emf_mode=0)
+              dz=0.1, gamma=5 / 3, ghost=3, precision=0, integrator=0, emf_mode=0, weights=0)
     kw.update(over)
     return wombat.GridDesc(**kw), dims
 
 
 @pytest.mark.parametrize("bad", [dict(ghost=2), dict(npatch=0), dict(dx=0.0), dict(gamma=1.0),
-                                 dict(precision=7), dict(integrator=5), dict(emf_mode=3)])
+                                 dict(precision=7), dict(integrator=5), dict(emf_mode=3),
+                                 dict(weights=2), dict(weights=1, precision=2)])
 def test_invalid_descriptor_is_rejected_on_the_host(lib, bad):
     from paper_1808_10633_gb300 import wombat
 

@@ -224,3 +224,76 @@ def test_fullsize_256_sampled_interfaces(orc, wb, prec, tol):
         err = (np.abs(got - ref) / scale).max()
         assert err <= tol, (axis, err)
     g.close()
+
+
+def test_patch_tile_shapes_and_autotune_match_oracle(orc, wb):
+    """Patches whose sizes make the cost model pick each of the three x-sweep
+    tile shapes inside one persistent launch; then the autotuner swaps tile
+    tables; both agree with the oracle patch by patch."""
+    rng = np.random.default_rng(17)
+    dims = [(16, 16, 8), (64, 4, 6), (32, 8, 8), (12, 20, 9)]
+    sts = [I.perturbed(*d, seed=40 + n, jump=True) for n, d in enumerate(dims)]
+    for s in sts:
+        s.dx = s.dy = s.dz = 1.0 / 32
+        s.U = I.assemble(*(s.U[0], s.U[1] / s.U[0], s.U[2] / s.U[0], s.U[3] / s.U[0],
+                           (s.U[7] - 0.5 * (s.U[1] ** 2 + s.U[2] ** 2 + s.U[3] ** 2) / s.U[0]
+                            - 0.5 * (s.U[4] ** 2 + s.U[5] ** 2 + s.U[6] ** 2)) * (s.gamma - 1),
+                           s.bx, s.by, s.bz, s.dx, s.dy, s.dz)).U
+    dt = 1e-3
+
+    def check(g):
+        U, b = g.get_state()
+        oU = ob = 0
+        for s in sts:
+            n = s.U[0].size
+            Uo, bxo, byo, bzo = orc.step(ogrid(orc, s), s.U, s.bx, s.by, s.bz, dt, nsteps=2)
+            assert rel_err(U[oU:oU + 8 * n].reshape(Uo.shape), Uo).max() <= TOL64
+            assert rel_err(b[ob:ob + 3 * n].reshape((3,) + s.shape), np.stack([bxo, byo, bzo])).max() <= TOL64
+            oU += 8 * n
+            ob += 3 * n
+
+    g = wb.Grid.from_patches(sts, precision="fp64")
+    g.step(dt, 2)
+    check(g)
+    g.set_state(np.concatenate([s.U.ravel() for s in sts]),
+                np.concatenate([np.stack([s.bx, s.by, s.bz]).ravel() for s in sts]))
+    ms = g.autotune()
+    assert ms.shape == (3, 4) and np.all(ms > 0)
+    g.step(dt, 2)
+    check(g)
+    g.close()
+
+
+def test_patch_batch_fp32_tracks_fp64(wb):
+    """Brio-Wu and turbulence patches of uneven sizes in one FP32 grid stay
+    finite and positive and track the FP64 path (L1 per field)."""
+    sts = I.patch_batch(12, seed=8, lo=16, hi=32)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        g = wb.Grid.from_patches(sts, precision=prec)
+        dt = g.cfl_dt(0.4) if prec == "fp64" else dt
+        g.step(dt, 10)
+        out[prec] = g.get_state()[0].reshape(-1)
+        g.close()
+    U64 = np.concatenate([u.reshape(8, -1) for u in np.split(out["fp64"], np.cumsum([8 * s.U[0].size for s in sts])[:-1])], axis=1)
+    U32 = np.concatenate([u.reshape(8, -1) for u in np.split(out["fp32"], np.cumsum([8 * s.U[0].size for s in sts])[:-1])], axis=1)
+    assert np.isfinite(U32).all() and U32[0].min() > 0
+    for f in range(8):
+        l1 = np.abs(U32[f] - U64[f]).mean() / max(np.abs(U64[f]).mean(), 1e-30)
+        assert l1 < 1e-4, (f, l1)
+
+
+def test_fp64_weno_z_weights_match_oracle(orc, wb):
+    st = I.perturbed(20, 16, 12, seed=77, jump=True)
+    g = wb.Grid.from_state(st, precision="fp64", weights="z")
+    g.step(2e-3, 2)
+    U, bx, by, bz = g.get_state_single()
+    g.close()
+    nx, ny, nz = st.dims
+    og = orc.Grid(nx, ny, nz, st.dx, st.dy, st.dz, st.gamma, 0, 1)
+    Uo, bxo, byo, bzo = orc.step(og, st.U, st.bx, st.by, st.bz, 2e-3, nsteps=2)
+    assert rel_err(U, Uo).max() <= TOL64
+    assert rel_err(np.stack([bx, by, bz]), np.stack([bxo, byo, bzo])).max() <= TOL64
+    # and they differ from the Jiang-Shu result
+    Uj = orc.step(ogrid(orc, st), st.U, st.bx, st.by, st.bz, 2e-3, nsteps=2)[0]
+    assert rel_err(Uj, Uo).max() > 1e3 * TOL64

@@ -127,3 +127,49 @@ def test_weno_flux_fifth_order_on_smooth_data(orc):
         errs.append(abs(deriv - np.cos(x0)))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders.min() > 4.5, (errs, orders)
+
+
+def test_weno_z_linear_data_and_brute_force_identity(orc):
+    """WENO-Z keeps the linear weights on linear data, and its phi_N obeys the
+    same reconstruction identity central - phi = sum_k omega_k q_k with the
+    brute-force candidates."""
+    g = golden()
+    cn = np.array(g["central_num"]) / g["central_den"][0]
+    for a in (0.0, 0.3, -2.0):
+        assert np.allclose(orc.weno_weights_z(a, a, a, a), g["linear_weights"], atol=1e-15)
+    rng = np.random.default_rng(21)
+    for _ in range(100):
+        f = rng.standard_normal(5)
+        q, _ = brute_candidates(f)
+        D = np.diff(f)
+        w = np.array(orc.weno_weights_z(*D))
+        got = float(np.dot(cn, f[1:5])) - orc.phi_n_z(*D)
+        assert got == pytest.approx(float(np.dot(w, q)), rel=1e-12, abs=1e-13)
+
+
+def test_critical_point_order_js_loss_and_weno_z(orc):
+    """Sec. 2.1: the Jiang-Shu scheme is only third order near critical
+    points; WENO-Z (the alternative it names) is not.  Max-norm error of the
+    flux-difference derivative on f = sin(pi x - sin(pi x)/pi), periodic on
+    [-1, 1], which has critical points with f'' != 0 (the test function of
+    Henrick, Aslam & Powers 2005)."""
+    g = golden()
+    cn = np.array(g["central_num"]) / g["central_den"][0]
+
+    def err(fn, N):
+        x = -1 + 2 * (np.arange(N) + 0.5) / N
+        h = 2.0 / N
+        f = np.sin(np.pi * x - np.sin(np.pi * x) / np.pi)
+        fp = np.cos(np.pi * x - np.sin(np.pi * x) / np.pi) * (np.pi - np.cos(np.pi * x))
+        F = np.empty(N)
+        for i in range(N):
+            st = np.array([f[(i + m) % N] for m in range(-2, 3)])
+            F[i] = float(np.dot(cn, st[1:5])) - fn(*np.diff(st))
+        return np.abs((F - np.roll(F, 1)) / h - fp).max()
+
+    ej = [err(orc.phi_n, N) for N in (80, 160, 320)]
+    ez = [err(orc.phi_n_z, N) for N in (80, 160, 320)]
+    oj = np.log2(ej[-2] / ej[-1])
+    oz = np.log2(ez[-2] / ez[-1])
+    assert 2.7 < oj < 3.5, (ej, oj)
+    assert oz > 3.9 and ez[-1] < 0.1 * ej[-1], (ez, oz)
