@@ -135,12 +135,11 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
 }
 
 // Weight policy of the classic scheme: Jiang-Shu weights for every field,
-// or the WENO-Z weights when z is set (uniform over the launch).
-template <class T>
+// or the WENO-Z weights when Z is set (a separate kernel instance).
+template <class T, bool Z = false>
 struct JsWeights {
-    bool z;
     __device__ __forceinline__ T corr(int, const T (&w)[6], const T (&g)[6], T alpha) {
-        return z ? weno_corr<T, true>(w, g, alpha) : weno_corr<T>(w, g, alpha);
+        return weno_corr<T, Z>(w, g, alpha);
     }
 };
 
@@ -622,7 +621,7 @@ __host__ __device__ constexpr int max_nc(int axis) {
 
 // One tile: stage the TA+5 cells of each of the TP pencils, then one thread
 // per interface.
-template <class T, int AXIS, int TA, int NCMAX>
+template <class T, int AXIS, int TA, int NCMAX, bool Z>
 __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& tile, const PatchDev& P,
                                           T* __restrict__ sm, int tid) {
     constexpr int TP = 256 / TA;
@@ -672,7 +671,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
     T F[7];
     T* bp = sm + kNSlot * NCMAX + tid;      // this thread's back-projection slots
-    JsWeights<T> js{A.zweights != 0};
+    JsWeights<T, Z> js;
     interface_flux<T>(sm, NC, id, T(A.gamma), bp, 256, js, F);
 
     // rotate back and store at the lower face of cell ia
@@ -699,7 +698,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
 // Persistent sweep: a grid of (SMs x resident blocks) strides over the tile
 // table; each tile is dispatched to the body of its shape (a block-uniform
 // branch), so patches of uneven sizes share one launch.
-template <class T, int AXIS>
+template <class T, int AXIS, bool Z>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
     constexpr int NCMAX = max_nc(AXIS);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -710,15 +709,15 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         const int shape = (unsigned)tile.x >> 24;
         tile.x &= 0xffffff;
         const PatchDev P = A.patches[tile.x];
-        if (shape == 0) tile_body<T, AXIS, shape_ta(AXIS, 0), NCMAX>(A, tile, P, sm, tid);
-        else if (shape == 1) tile_body<T, AXIS, shape_ta(AXIS, 1), NCMAX>(A, tile, P, sm, tid);
-        else tile_body<T, AXIS, shape_ta(AXIS, 2), NCMAX>(A, tile, P, sm, tid);
+        if (shape == 0) tile_body<T, AXIS, shape_ta(AXIS, 0), NCMAX, Z>(A, tile, P, sm, tid);
+        else if (shape == 1) tile_body<T, AXIS, shape_ta(AXIS, 1), NCMAX, Z>(A, tile, P, sm, tid);
+        else tile_body<T, AXIS, shape_ta(AXIS, 2), NCMAX, Z>(A, tile, P, sm, tid);
         __syncthreads();
     }
 }
 
-// One tile per block, default shape: the launch for tile tables that use
-// shape 0 throughout (a single grid, or patches tuned to it).
+// One tile per block, default shape, Jiang-Shu weights: the launch for tile
+// tables that use shape 0 throughout (a single grid, or patches tuned to it).
 template <class T, int AXIS>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel_fixed(const SweepArgs<T> A) {
     constexpr int NC0 = nc_of(shape_ta(AXIS, 0));
@@ -727,7 +726,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel_fixed(c
     Tile tile = A.tiles[blockIdx.x];
     tile.x &= 0xffffff;
     const PatchDev P = A.patches[tile.x];
-    tile_body<T, AXIS, shape_ta(AXIS, 0), NC0>(A, tile, P, sm, threadIdx.x);
+    tile_body<T, AXIS, shape_ta(AXIS, 0), NC0, false>(A, tile, P, sm, threadIdx.x);
 }
 
 template <class T, int AXIS>
@@ -760,24 +759,33 @@ template <class T>
 int sweep_blocks_per_sm(int axis) {
     int nb = 0;
     if (axis == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 0>, 256, smem_bytes_persistent<T, 0>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 0, false>, 256, smem_bytes_persistent<T, 0>());
     else if (axis == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 1>, 256, smem_bytes_persistent<T, 1>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 1, false>, 256, smem_bytes_persistent<T, 1>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 2>, 256, smem_bytes_persistent<T, 2>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 2, false>, 256, smem_bytes_persistent<T, 2>());
     return nb > 0 ? nb : 1;
 }
 
 template <class T>
 cudaError_t prepare_sweep_kernels() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(sweep_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sweep_kernel<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes_persistent<T, 0>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sweep_kernel<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_persistent<T, 0>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes_persistent<T, 1>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sweep_kernel<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_persistent<T, 1>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_persistent<T, 2>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes_persistent<T, 2>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -799,7 +807,7 @@ cudaError_t prepare_sweep_kernels() {
 template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (a.uniform_shape0) {
+    if (a.uniform_shape0 && !a.zweights) {
         if (axis == 0) sweep_kernel_fixed<T, 0><<<ntiles, 256, smem_bytes_fixed<T, 0>(), s>>>(a);
         else if (axis == 1) sweep_kernel_fixed<T, 1><<<ntiles, 256, smem_bytes_fixed<T, 1>(), s>>>(a);
         else sweep_kernel_fixed<T, 2><<<ntiles, 256, smem_bytes_fixed<T, 2>(), s>>>(a);
@@ -807,9 +815,15 @@ cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream
     }
     const int grid = PersistGrid<T>::g[axis] > 0 ? PersistGrid<T>::g[axis] : 152;
     const int nb = ntiles < grid ? ntiles : grid;
-    if (axis == 0) sweep_kernel<T, 0><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
-    else if (axis == 1) sweep_kernel<T, 1><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
-    else sweep_kernel<T, 2><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
+    if (a.zweights) {
+        if (axis == 0) sweep_kernel<T, 0, true><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
+        else if (axis == 1) sweep_kernel<T, 1, true><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
+        else sweep_kernel<T, 2, true><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
+        return cudaGetLastError();
+    }
+    if (axis == 0) sweep_kernel<T, 0, false><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
+    else if (axis == 1) sweep_kernel<T, 1, false><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
+    else sweep_kernel<T, 2, false><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
     return cudaGetLastError();
 }
 
