@@ -227,6 +227,11 @@ def run_native(args, rank, world, local):
     if args.patches > 0:
         patches = run_patches(args, world)
 
+    # ---- 512^3 turbulence + blasts, sweep kernels only (config 3) -----------
+    large = None
+    if args.large_size > 0:
+        large = run_large(args, world)
+
     # ---- learned weights on turbulence + blasts (config 5) -----------------
     learned = None
     if not args.no_learned:
@@ -284,6 +289,7 @@ def run_native(args, rank, world, local):
         "e2e": e2e,
         "learned": learned,
         "patches": patches,
+        "large": large,
     })
     return out
 
@@ -328,6 +334,46 @@ def run_patches(args, world):
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
                             "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]},
+            "generate_s": t_gen}
+
+
+def run_large(args, world):
+    """512^3 turbulence with 64 blast spheres (p x100, radii 0.02-0.05) in
+    FP32 with FP64 islands; the rate counts the three sweep kernels only."""
+    import torch
+
+    from paper_1808_10633_gb300 import inputs, wombat
+
+    n = args.large_size
+    t0 = time.perf_counter()
+    st = inputs.add_blasts(inputs.turbulence(n, seed=1808), seed=1808, nblast=64)
+    t_gen = time.perf_counter() - t0
+    g = wombat.Grid.from_state(st, precision="fp32")
+    blast_cells = st.meta.get("blast_cells")
+    del st
+    steps = max(2, args.large_steps)
+    for _ in range(args.warmup):
+        g.step_cfl(args.cfl, 1)
+    g.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    tot, kms, kcnt = g.step_profiled(args.cfl, steps, with_totals=True)
+    barrier(world)
+    sweep_ms = sum(kms[k] for k in ("sweep_x", "sweep_y", "sweep_z"))
+    sweep_s = max_over_ranks(sweep_ms / 1e3, world)
+    secs = max_over_ranks(tot / 1e3, world)
+    try:
+        finite = bool(np.isfinite(g.totals()).all())
+    except wombat.WombatError:
+        finite = False
+    g.close()
+    zones = n ** 3
+    return {"workload": f"turbulence {n}^3 + 64 blast spheres (p x100, r 0.02-0.05), FP32 with FP64 islands",
+            "value_sweeps_only": world * zones * steps / sweep_s,
+            "value_whole_step": world * zones * steps / secs, "unit": UNIT, "steps": steps,
+            "sweep_ms_per_step": sweep_s * 1e3 / steps,
+            "kernel_ms_per_step": {k: v / steps for k, v in kms.items()},
+            "blast_cells": blast_cells, "finite_after": finite,
             "generate_s": t_gen}
 
 
@@ -465,7 +511,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-weights leg")
-    ap.add_argument("--patches", type=int, default=512,
+    ap.add_argument("--large-size", type=int, default=512,
+                    help="edge of the turbulence + blasts leg timed on its sweeps (0: skip)")
+    ap.add_argument("--large-steps", type=int, default=10)
+    ap.add_argument("--patches", type=int, default=4096,
                     help="patch count of the batched-patch leg (0: skip)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")

@@ -14,6 +14,7 @@ permeability absorbed (magnetic pressure |B|^2/2).
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -124,19 +125,51 @@ def alfven_wave(nx, ny=4, nz=4, amp=0.1, rho=1.0, p=0.1, b_par=1.0, t=0.0,
                     {"kind": "alfven", "amp": amp, "t": t})
 
 
+@functools.lru_cache(maxsize=None)
+def _modes(kmin, kmax):
+    """Integer wavevectors (kx, ky, kz) with kmin <= |k| <= kmax in the half
+    space (kx > 0, or kx = 0 and ky > 0, or kx = ky = 0 and kz > 0), in a
+    fixed order that does not depend on the grid."""
+    K = int(np.floor(kmax))
+    out = []
+    for kx in range(0, K + 1):
+        for ky in range(-K, K + 1):
+            for kz in range(-K, K + 1):
+                if kx == 0 and (ky < 0 or (ky == 0 and kz <= 0)):
+                    continue
+                k2 = kx * kx + ky * ky + kz * kz
+                if kmin * kmin <= k2 <= kmax * kmax:
+                    out.append((kx, ky, kz))
+    out = np.array(out, dtype=np.int64).reshape(-1, 3)
+    out.setflags(write=False)
+    return out
+
+
 def gaussian_field(shape, rng, kmin=1.0, kmax=8.0, slope=-11.0 / 3.0):
     """Unit-variance Gaussian random field on a periodic grid.
 
-    Each Fourier mode with integer wavenumber kmin <= |k| <= kmax (units of
-    2 pi / box) gets a complex Gaussian amplitude of variance |k|^slope."""
+    A sum of Fourier modes with integer wavevector kmin <= |k| <= kmax (units
+    of 2 pi / box), each with a complex Gaussian amplitude of variance
+    |k|^slope (random phase), plus its conjugate.  The amplitudes are drawn
+    per mode in a grid-independent order, so one seed gives the same
+    continuous field at every resolution; it is evaluated on the cell grid
+    by three separable partial sums (x, then y, then z as a matrix
+    product) and scaled to zero mean and unit variance over the grid."""
     nz, ny, nx = shape
-    kz = np.fft.fftfreq(nz, d=1.0 / nz)[:, None, None]
-    ky = np.fft.fftfreq(ny, d=1.0 / ny)[None, :, None]
-    kx = np.fft.rfftfreq(nx, d=1.0 / nx)[None, None, :]
-    k = np.sqrt(kx * kx + ky * ky + kz * kz)
-    amp = np.where((k >= kmin) & (k <= kmax), np.power(np.maximum(k, 1e-30), slope / 2.0), 0.0)
-    noise = rng.standard_normal(amp.shape) + 1j * rng.standard_normal(amp.shape)
-    f = np.fft.irfftn(noise * amp, s=shape, axes=(0, 1, 2))
+    ks = _modes(kmin, kmax)
+    K = int(np.floor(kmax))
+    a = rng.standard_normal(len(ks)) + 1j * rng.standard_normal(len(ks))
+    a *= np.power(np.sqrt((ks * ks).sum(axis=1)).astype(float), slope / 2.0)
+    C = np.zeros((2 * K + 1, 2 * K + 1, K + 1), dtype=complex)     # [kz, ky, kx]
+    C[ks[:, 2] + K, ks[:, 1] + K, ks[:, 0]] = 2.0 * a               # mode plus conjugate
+    ex = np.exp(2j * np.pi * np.outer(np.arange(K + 1), np.arange(nx)) / nx)          # [kx, x]
+    ey = np.exp(2j * np.pi * np.outer(np.arange(ny), np.arange(-K, K + 1)) / ny)      # [y, ky]
+    ez = np.exp(2j * np.pi * np.outer(np.arange(nz), np.arange(-K, K + 1)) / nz)      # [z, kz]
+    T1 = C @ ex                                           # [kz, ky, x]
+    T2 = np.matmul(ey[None], T1)                          # [kz, y, x]
+    T2 = T2.reshape(2 * K + 1, ny * nx)
+    f = ez.real @ T2.real - ez.imag @ T2.imag             # real part, [z, y*x]
+    f = f.reshape(nz, ny, nx)
     f -= f.mean()
     s = f.std()
     return f / s if s > 0 else f
@@ -180,26 +213,40 @@ def turbulence(n, seed=1808, mach=0.5, sigma_rho=0.1, p=1.0, b0=0.1, eb_frac=0.1
 def add_blasts(st: State, seed=1808, nblast=64, rmin=0.02, rmax=0.05, jump=100.0) -> State:
     """Multiply the pressure by `jump` inside `nblast` seeded spheres (periodic
     distance, uniform centres, radii uniform in [rmin, rmax]; overlaps keep one
-    jump).  The kinetic and magnetic parts of E are unchanged."""
+    jump).  The kinetic and magnetic parts of E are unchanged.  Each sphere
+    is marked inside the periodic box of cells that bounds it."""
     st = st.copy()
     nx, ny, nz = st.dims
     rng = np.random.default_rng(seed + 7919)
-    X, Y, Z = _centres(nx, ny, nz, st.dx, st.dy, st.dz)
-    Lx, Ly, Lz = nx * st.dx, ny * st.dy, nz * st.dz
+    h = (st.dx, st.dy, st.dz)
+    L = (nx * st.dx, ny * st.dy, nz * st.dz)
+    n = (nx, ny, nz)
     inside = np.zeros(st.shape, dtype=bool)
     for _ in range(nblast):
-        c = rng.uniform(0.0, 1.0, 3) * (Lx, Ly, Lz)
+        c = rng.uniform(0.0, 1.0, 3) * L
         r = rng.uniform(rmin, rmax)
-        ddx = np.abs(X - c[0]); ddx = np.minimum(ddx, Lx - ddx)
-        ddy = np.abs(Y - c[1]); ddy = np.minimum(ddy, Ly - ddy)
-        ddz = np.abs(Z - c[2]); ddz = np.minimum(ddz, Lz - ddz)
-        inside |= ddx * ddx + ddy * ddy + ddz * ddz < r * r
+        idx, d2 = [], []
+        for d in range(3):
+            lo = int(np.floor((c[d] - r) / h[d] - 0.5)) - 1
+            hi = int(np.ceil((c[d] + r) / h[d] - 0.5)) + 1
+            cells = np.arange(lo, hi + 1)
+            if len(cells) >= n[d]:
+                cells = np.arange(n[d])
+            x = (np.mod(cells, n[d]) + 0.5) * h[d]
+            dd = np.abs(x - c[d])
+            dd = np.minimum(dd, L[d] - dd)
+            idx.append(np.mod(cells, n[d]))
+            d2.append(dd * dd)
+        ball = d2[2][:, None, None] + d2[1][None, :, None] + d2[0][None, None, :] < r * r
+        sub = np.ix_(idx[2], idx[1], idx[0])
+        inside[sub] |= ball
     U = st.U
-    kin = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
-    mag = 0.5 * (U[4] ** 2 + U[5] ** 2 + U[6] ** 2)
-    pth = (U[7] - kin - mag) * (st.gamma - 1.0)
-    pth = np.where(inside, pth * jump, pth)
-    U[7] = pth / (st.gamma - 1.0) + kin + mag
+    sel = np.nonzero(inside)
+    Us = U[(slice(None),) + sel]
+    kin = 0.5 * (Us[1] ** 2 + Us[2] ** 2 + Us[3] ** 2) / Us[0]
+    mag = 0.5 * (Us[4] ** 2 + Us[5] ** 2 + Us[6] ** 2)
+    pth = (Us[7] - kin - mag) * (st.gamma - 1.0)
+    U[(7,) + sel] = pth * jump / (st.gamma - 1.0) + kin + mag
     st.meta = dict(st.meta, blasts=nblast, blast_cells=int(inside.sum()))
     return st
 

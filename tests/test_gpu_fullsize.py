@@ -1,0 +1,116 @@
+"""Full-size workloads in the benchmark's launch configuration, checked on
+sampled outputs that the oracle computes one at a time.
+
+- 512^3 decaying turbulence with 64 blast spheres (pressure x100), FP32 with
+  FP64 islands: eq. FWENO fluxes at random interfaces and at interfaces
+  across blast edges, against the oracle's single-interface flux.
+- 4096 periodic patches with edges log-uniform in [16, 64], each a rotated
+  Brio-Wu tube or a turbulence state, FP32 in one persistent launch per axis
+  with autotuned tile shapes: one CFL step, then whole patches against the
+  oracle's step of the same patch.
+
+FP32 tolerances.  A flux sample's components mix through the characteristic
+projection, so each is held to 1e-4 of that component's scale plus 4e-6 of
+the sample's largest component (about thirty FP32 ulps of it): at a blast
+edge the energy flux is a thousand times the field fluxes.  Turbulence
+patches are held to 1e-4 of each field's largest magnitude after one step.
+Rotated Brio-Wu tubes are held to 1e-3 in the L1 norm of the whole state and
+to FP32 round-off in their conserved sums: where the tangential field
+reverses across a jump the eigenvector normalisation direction (beta_y,
+beta_z) turns with values at rounding level (the B_perp -> 0 rule), so FP32
+and FP64 reach different, equally valid, results there."""
+import numpy as np
+import pytest
+
+from paper_1808_10633_gb300 import inputs as I
+from sampling import oracle_face_flux
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def wb():
+    from paper_1808_10633_gb300 import build, wombat
+
+    build.build()
+    return wombat
+
+
+def rel_err(gpu, ref):
+    floor = 1e-3 * max(np.abs(ref).max(), 1e-300)
+    return np.array([np.abs(gpu[f] - ref[f]).max() / max(np.abs(ref[f]).max(), floor)
+                     for f in range(gpu.shape[0])])
+
+
+def test_fullsize_512_blasts_sampled_interfaces(orc, wb):
+    st = I.add_blasts(I.turbulence(512, seed=1808), seed=1808, nblast=64)
+    g = wb.Grid.from_state(st, precision="fp32")
+    rng = np.random.default_rng(512)
+    nx, ny, nz = st.dims
+    E = st.U[7]
+    worst = []
+    for axis in range(3):
+        # interfaces i-1/2 whose two cells differ in E by more than 5x: blast edges
+        jump = np.abs(np.log(E / np.roll(E, 1, axis=2 - axis))) > np.log(5.0)
+        kk, jj, ii = np.nonzero(jump)
+        del jump
+        assert len(ii) > 1000
+        pick = rng.choice(len(ii), 100, replace=False)
+        idx = np.concatenate([rng.integers(0, [nx, ny, nz], size=(100, 3)),
+                              np.stack([ii[pick], jj[pick], kk[pick]], axis=1)])
+        F = g.face_fluxes(axis)
+        got = np.empty((len(idx), 7))
+        ref = np.empty((len(idx), 7))
+        for r, (i, j, k) in enumerate(idx):
+            got[r] = F[:, (k * ny + j) * nx + i]
+            ref[r] = oracle_face_flux(orc, st, axis, i, j, k)
+        del F
+        scale = np.abs(ref).max(axis=0)[None, :]
+        rowmax = np.abs(ref).max(axis=1)[:, None]
+        ratio = np.abs(got - ref) / (TOL32 * scale + 4e-6 * rowmax)
+        worst.append(float(ratio.max()))
+        assert ratio.max() <= 1.0, (axis, ratio.max(), np.unravel_index(ratio.argmax(), ratio.shape))
+    g.close()
+    print("512^3 blasts, worst error / tolerance per axis:", worst)
+
+
+def test_fullsize_4096_patches_sampled(orc, wb):
+    sts = I.patch_batch(4096, seed=1808)
+    g = wb.Grid.from_patches(sts, precision="fp32")
+    ms = g.autotune()
+    assert ms.shape == (3, 4) and np.all(ms > 0)
+    dt = g.cfl_dt(0.4)
+    g.step(dt, 1)
+    U, b = g.get_state()
+    g.close()
+    ncell = np.array([s.U[0].size for s in sts])
+    offU = np.concatenate([[0], np.cumsum(8 * ncell)])
+    offb = np.concatenate([[0], np.cumsum(3 * ncell)])
+    rng = np.random.default_rng(4096)
+    kinds = np.array([s.meta.get("kind") for s in sts])
+    picks = set(rng.choice(np.nonzero(kinds == "brio_wu")[0], 4, replace=False).tolist())
+    picks |= set(rng.choice(np.nonzero(kinds == "turbulence")[0], 4, replace=False).tolist())
+    picks |= {int(ncell.argmin()), int(ncell.argmax())}
+    report = []
+    for p in sorted(picks):
+        s = sts[p]
+        nx, ny, nz = s.dims
+        og = orc.Grid(nx, ny, nz, s.dx, s.dy, s.dz, s.gamma)
+        Uo, bxo, byo, bzo = orc.step(og, s.U, s.bx, s.by, s.bz, dt, nsteps=1)
+        Ug = U[offU[p]:offU[p + 1]].reshape(Uo.shape)
+        bg = b[offb[p]:offb[p + 1]].reshape((3,) + s.shape)
+        bo = np.stack([bxo, byo, bzo])
+        kind = s.meta.get("kind")
+        if kind == "turbulence":
+            e = max(rel_err(Ug, Uo).max(), rel_err(bg, bo).max())
+            report.append((p, kind, s.dims, float(e)))
+            assert e <= TOL32, report[-1]
+        else:
+            l1 = (np.abs(Ug - Uo).sum() + np.abs(bg - bo).sum()) / (np.abs(Uo).sum() + np.abs(bo).sum())
+            mass = [abs(Ug[f].sum() - Uo[f].sum()) / np.abs(Uo[f]).sum().clip(1e-300) for f in (0, 7)]
+            flux = [abs(bg[d].sum() - bo[d].sum()) / np.abs(bo[d]).sum().clip(1e-300) for d in range(3)]
+            report.append((p, kind, s.dims, float(l1), float(max(mass + flux))))
+            assert l1 <= 1e-3 and max(mass + flux) <= 1e-6, report[-1]
+    print("4096 patches, sampled patches:", report)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_1808_10633_gb300 import inputs as I
+from sampling import oracle_face_flux
 
 pytestmark = pytest.mark.gpu
 
@@ -179,29 +180,6 @@ def test_nonfinite_state_is_reported(wb):
     g.close()
 
 
-def _oracle_face_flux(orc, st, axis, i, j, k):
-    """Oracle eq. FWENO flux through the lower face of cell (i, j, k) along
-    axis, in the library's component order (rho, mx, my, mz, E, B_t1, B_t2)."""
-    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
-    perm = [0, 1 + n, 1 + t1, 1 + t2, 4 + n, 4 + t1, 4 + t2, 7]
-    nx, ny, nz = st.dims
-    dims = (nx, ny, nz)
-    Us = np.empty((6, 8))
-    for m in range(6):
-        q = [i, j, k]
-        q[axis] = (q[axis] + m - 3) % dims[axis]
-        Us[m] = st.U[perm, q[2], q[1], q[0]]
-    Fh = orc.interface_flux(Us, st.gamma)
-    out = np.empty(7)
-    out[0] = Fh[0]
-    for gq in range(3):
-        out[1 + gq] = Fh[perm.index(1 + gq)]
-    out[4] = Fh[7]
-    out[5] = Fh[5]
-    out[6] = Fh[6]
-    return out
-
-
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
 def test_fullsize_256_sampled_interfaces(orc, wb, prec, tol):
     """At the benchmark's 256^3 turbulence size, in the benchmark's launch
@@ -219,7 +197,7 @@ def test_fullsize_256_sampled_interfaces(orc, wb, prec, tol):
         for r, (i, j, k) in enumerate(idx):
             c = (k * ny + j) * nx + i
             got[r] = F[:, c]
-            ref[r] = _oracle_face_flux(orc, st, axis, i, j, k)
+            ref[r] = oracle_face_flux(orc, st, axis, i, j, k)
         scale = np.maximum(np.abs(ref).max(axis=0), 1e-3 * np.abs(ref).max())
         err = (np.abs(got - ref) / scale).max()
         assert err <= tol, (axis, err)
