@@ -438,7 +438,7 @@ void orc_face_fluxes(const orc_grid *g, const double *U, int axis, double *F)
     int n = axis, t1 = (axis + 1) % 3, t2 = (axis + 2) % 3;
     int perm[8] = {0, 1 + n, 1 + t1, 1 + t2, 4 + n, 4 + t1, 4 + t2, 7};
     int dims[3] = {g->nx, g->ny, g->nz};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->nz; k++)
         for (int j = 0; j < g->ny; j++)
             for (int i = 0; i < g->nx; i++) {
@@ -482,7 +482,7 @@ static void edge_emfs(const orc_grid *g, const double *U, const double *Fx,
 {
     long N = ncell(g);
     int nx = g->nx, ny = g->ny, nz = g->nz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; k++)
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
@@ -535,7 +535,7 @@ void orc_rhs(const orc_grid *g, const double *U, double *LU, double *Lb,
     orc_face_fluxes(g, U, 1, Fy);
     orc_face_fluxes(g, U, 2, Fz);
     static const int CQ[5] = {0, 1, 2, 3, 7};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; k++)
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
@@ -559,7 +559,7 @@ void orc_rhs(const orc_grid *g, const double *U, double *LU, double *Lb,
     double *Ey = (double *)malloc(sizeof(double) * N);
     double *Ez = (double *)malloc(sizeof(double) * N);
     edge_emfs(g, U, Fx, Fy, Fz, Ex, Ey, Ez);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; k++)
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {

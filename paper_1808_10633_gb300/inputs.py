@@ -305,6 +305,44 @@ def brio_wu_patch(dims, rng, bn=0.75, gamma=GAMMA, h=None) -> State:
                     {"kind": "brio_wu", "normal": nvec.tolist(), "m": m.tolist()})
 
 
+def field_loop(n, amp=1e-3, radius=0.3, v=(1.0, 1.0), rho=1.0, p=1.0, gamma=GAMMA) -> State:
+    """Advected weak field loop on the periodic unit square (n x n x 1).
+
+    A_z = amp (R - r) inside the radius R around the box centre, zero
+    outside; b = curl A (face divergence zero); uniform rho, p and velocity,
+    so the loop returns to its start after t = 1 with v = (1, 1)."""
+    h = 1.0 / n
+    x = np.arange(n) * h                        # edge positions (i - 1/2) * h + h/2
+    X, Y = np.meshgrid(x, x, indexing="xy")     # [j, i]
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    Az = np.where(r < radius, amp * (radius - r), 0.0)[None, :, :]
+    zero = np.zeros((1, n, n))
+    bx, by, bz = curl_faces(zero, zero, Az, h, h, h)
+    return assemble(np.full((1, n, n), rho), v[0], v[1], 0.0, p, bx, by, bz, h, h, h, gamma,
+                    {"kind": "field_loop", "n": n, "amp": amp, "radius": radius})
+
+
+def orszag_tang(n, gamma=GAMMA) -> State:
+    """Orszag-Tang vortex on the periodic unit square (n x n x 1), in units
+    with the permeability absorbed: rho = 25/(36 pi), p = 5/(12 pi),
+    v = (-sin 2 pi y, sin 2 pi x), B = B0 (-sin 2 pi y, sin 4 pi x) with
+    B0 = 1/sqrt(4 pi), the field from A_z = B0 (cos 4 pi x / (4 pi) +
+    cos 2 pi y / (2 pi))."""
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    xe = np.arange(n) * h
+    B0 = 1.0 / np.sqrt(4.0 * np.pi)
+    Xe, Ye = np.meshgrid(xe, xe, indexing="xy")
+    Az = (B0 * (np.cos(4.0 * np.pi * Xe) / (4.0 * np.pi) + np.cos(2.0 * np.pi * Ye) / (2.0 * np.pi)))[None]
+    zero = np.zeros((1, n, n))
+    bx, by, bz = curl_faces(zero, zero, Az, h, h, h)
+    Xc, Yc = np.meshgrid(xc, xc, indexing="xy")
+    vx = -np.sin(2.0 * np.pi * Yc)[None]
+    vy = np.sin(2.0 * np.pi * Xc)[None]
+    return assemble(np.full((1, n, n), 25.0 / (36.0 * np.pi)), vx, vy, 0.0, 5.0 / (12.0 * np.pi),
+                    bx, by, bz, h, h, h, gamma, {"kind": "orszag_tang", "n": n})
+
+
 def patch_dims(npatch, seed=1808, lo=16, hi=64, max_aspect=2.0):
     """Patch edges drawn independently log-uniform in [lo, hi]; a draw whose
     longest/shortest edge exceeds max_aspect is redrawn."""
