@@ -26,7 +26,8 @@
  *     |B|^2/2 (magnetic permeability absorbed).  Face arrays use
  *     [patch][3][nz][ny][nx]: component 0 is b_x on the face (i-1/2, j, k),
  *     1 is b_y on (i, j-1/2, k), 2 is b_z on (i, j, k-1/2).  Each patch is
- *     periodic in every direction.  The cell-centred B is always the mean of
+ *     periodic in every direction, unless wb_grid_desc.links joins patches
+ *     into a larger world.  The cell-centred B is always the mean of
  *     the two faces: the B entries of a cell array passed in are ignored and
  *     those returned are recomputed from the faces.
  *   - Values are FP64 at the ABI in every precision mode.
@@ -81,6 +82,21 @@ typedef struct {
     int weights;          /* 0: Jiang-Shu nonlinear weights (Sec. 2.1);
                              1: WENO-Z weights (the alternative Sec. 2.1
                              names); not with WB_FP32_LEARNED              */
+    const int *links;     /* NULL: every patch is periodic on itself.
+                             Otherwise host, npatch*27 patch indices, copied:
+                             links[27 p + 9 (oz+1) + 3 (oy+1) + (ox+1)] is
+                             the patch that continues patch p in direction
+                             (ox, oy, oz) in {-1,0,1}^3, so patches tile a
+                             larger world and read their neighbours' cells
+                             in place where Sec. 2.2 fills ghost zones.
+                             Checked: entries in [0, npatch), centre entry
+                             p, reciprocal, diagonal entries the composition
+                             of single-axis moves, equal extents along the
+                             axes a link does not cross, and at least 3 cells
+                             on both sides of every crossing between two
+                             different patches; else WB_EINVAL.  A patch may
+                             link to itself along an axis (periodic there).
+                             wb_harvest needs links == NULL.               */
 } wb_grid_desc;
 
 typedef struct {
@@ -99,8 +115,8 @@ typedef struct {
  * cudaStream_t to order all work on, or NULL for a stream the library
  * creates.  out: receives the grid.  Synchronises.
  * Errors: WB_EINVAL for a null pointer, npatch < 1, a size out of range,
- * ghost != 3, an unknown mode, WENO-Z with learned weights, or
- * non-positive dx/dy/dz or gamma <= 1;
+ * ghost != 3, an unknown mode, WENO-Z with learned weights,
+ * non-positive dx/dy/dz or gamma <= 1, or an inconsistent link table;
  * WB_ENOMEM; WB_ECUDA. */
 int wb_init_grid(const wb_grid_desc *d, const double *U0, const double *b0,
                  void *cuda_stream, wb_grid **out);

@@ -91,6 +91,7 @@ struct wb_grid {
     int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
     wb::PatchDev* d_patches = nullptr;
     std::vector<wb::PatchDev> h_patches;
+    int* d_links = nullptr;               // 27 per patch (wb::locate) or nullptr
     wb::Tile* d_tiles[3] = {nullptr, nullptr, nullptr};
     int ntiles[3] = {0, 0, 0};
     wb::CellBlock* d_blocks = nullptr;
@@ -128,6 +129,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.er = (axis == 0 && g->emf_mode == 0) ? er : nullptr;
             a.tiles = g->d_tiles[axis];
             a.patches = g->d_patches;
+    a.links = g->d_links;
             a.ncells = N;
             a.gamma = g->gamma;
             a.zweights = g->weights;
@@ -154,6 +156,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
         u.er = g->emf_mode == 0 ? er : nullptr;
         u.blocks = g->d_blocks;
         u.patches = g->d_patches;
+        u.links = g->d_links;
         u.dt = g->d_scalars;
         u.ncells = N;
         u.idx = 1.0 / g->dx;
@@ -179,11 +182,11 @@ int enqueue_cfl(wb_grid* g, Prof* pf = nullptr) {
     if (rc != WB_OK) return rc;
     WB_CK(cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->stream));
     if (g->precision == WB_FP64)
-        WB_CK(wb::launch_cfl<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches,
+        WB_CK(wb::launch_cfl<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches, g->d_links,
                                      g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
                                      g->gamma, g->d_smax, g->d_flag, g->stream));
     else
-        WB_CK(wb::launch_cfl<float>(static_cast<const float*>(g->un), g->d_blocks, g->d_patches,
+        WB_CK(wb::launch_cfl<float>(static_cast<const float*>(g->un), g->d_blocks, g->d_patches, g->d_links,
                                     g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
                                     g->gamma, g->d_smax, g->d_flag, g->stream));
     return prof_end(pf, g->stream, WB_K_CFL);
@@ -285,7 +288,8 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_patches, g->d_tiles[0],
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_patches, g->d_links,
+                    g->d_tiles[0],
                     g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_scalars, g->d_smax,
                     g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
@@ -336,6 +340,61 @@ std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
     return out;
 }
 
+// Checks a patch link table (layout of wb::locate): every entry names a
+// patch, the centre entry is the patch itself, links are reciprocal, a
+// diagonal link is the composition of single-axis moves in any order,
+// linked patches agree in their extents along the axes they are not offset
+// in, and a patch met across an axis from a different patch is at least 3
+// cells deep along it (the stencil reach), as is the patch left behind.
+int check_links(const std::vector<wb::PatchDev>& P, const int* L) {
+    const long long n = (long long)P.size();
+    auto at = [&](long long p, int ox, int oy, int oz) {
+        return L[27 * p + 9 * (oz + 1) + 3 * (oy + 1) + (ox + 1)];
+    };
+    auto ext = [&](long long p, int d) { return d == 0 ? P[p].nx : (d == 1 ? P[p].ny : P[p].nz); };
+    for (long long p = 0; p < n; p++)
+        for (int oz = -1; oz <= 1; oz++)
+            for (int oy = -1; oy <= 1; oy++)
+                for (int ox = -1; ox <= 1; ox++) {
+                    const int q = at(p, ox, oy, oz);
+                    if (q < 0 || q >= n)
+                        return fail(WB_EINVAL, "links: patch %lld direction (%d,%d,%d) names patch %d",
+                                    p, ox, oy, oz, q);
+                }
+    for (long long p = 0; p < n; p++) {
+        if (at(p, 0, 0, 0) != p) return fail(WB_EINVAL, "links: centre entry of patch %lld is not itself", p);
+        for (int oz = -1; oz <= 1; oz++)
+            for (int oy = -1; oy <= 1; oy++)
+                for (int ox = -1; ox <= 1; ox++) {
+                    if (!ox && !oy && !oz) continue;
+                    const int o[3] = {ox, oy, oz};
+                    const int q = at(p, ox, oy, oz);
+                    if (at(q, -ox, -oy, -oz) != p)
+                        return fail(WB_EINVAL, "links: patch %lld -> %d along (%d,%d,%d) is not reciprocal",
+                                    p, q, ox, oy, oz);
+                    for (int d = 0; d < 3; d++) {
+                        if (o[d] == 0) {
+                            if (ext(q, d) != ext(p, d))
+                                return fail(WB_EINVAL, "links: patches %lld and %d differ in extent %d",
+                                            p, q, d);
+                            continue;
+                        }
+                        int e[3] = {0, 0, 0}, r[3] = {ox, oy, oz};
+                        e[d] = o[d];
+                        r[d] = 0;
+                        const int f = at(p, e[0], e[1], e[2]);
+                        if (at(f, r[0], r[1], r[2]) != q)
+                            return fail(WB_EINVAL, "links: patch %lld direction (%d,%d,%d) is not the "
+                                        "composition of its moves", p, ox, oy, oz);
+                        if (f != p && (ext(p, d) < 3 || ext(f, d) < 3))
+                            return fail(WB_EINVAL, "links: patches %lld and %d meet along axis %d with "
+                                        "fewer than 3 cells", p, f, d);
+                    }
+                }
+    }
+    return WB_OK;
+}
+
 // 1 when every tile uses shape 0 (then one tile per block, no dispatch).
 int tiles_uniform(const std::vector<wb::Tile>& t) {
     for (const wb::Tile& x : t)
@@ -360,6 +419,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     a.er = nullptr;
     a.tiles = g->d_tiles[axis];
     a.patches = g->d_patches;
+    a.links = g->d_links;
     a.ncells = N;
     a.gamma = g->gamma;
     a.zweights = g->weights;
@@ -392,6 +452,7 @@ int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, int unif
     a.er = nullptr;
     a.tiles = tiles;
     a.patches = g->d_patches;
+    a.links = g->d_links;
     a.ncells = g->N;
     a.gamma = g->gamma;
     a.zweights = g->weights;
@@ -466,6 +527,13 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
         off += np;
     }
     g->N = off;
+    if (d->links) {
+        const int lrc = check_links(g->h_patches, d->links);
+        if (lrc != WB_OK) {
+            delete g;
+            return lrc;
+        }
+    }
 
     int rc;
     auto bail = [&](int code) { release(g); return code; };
@@ -508,6 +576,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (g->emf_mode == 0 && (rc = dmalloc(g, &g->er, T * 3 * N))) return bail(rc);
     if ((rc = dmalloc(g, &g->emf, T * 3 * N))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_patches, sizeof(wb::PatchDev) * g->npatch))) return bail(rc);
+    if (d->links && (rc = dmalloc(g, &g->d_links, sizeof(int) * 27 * (size_t)g->npatch))) return bail(rc);
     for (int a = 0; a < 3; a++)
         if ((rc = dmalloc(g, &g->d_tiles[a], sizeof(wb::Tile) * tiles[a].size()))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_blocks, sizeof(wb::CellBlock) * blocks.size()))) return bail(rc);
@@ -522,6 +591,8 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream);
     };
+    if (d->links && cp(g->d_links, d->links, sizeof(int) * 27 * (size_t)g->npatch) != cudaSuccess)
+        return bail(fail(WB_ECUDA, "link upload failed"));
     if (cp(g->d_patches, g->h_patches.data(), sizeof(wb::PatchDev) * g->npatch) != cudaSuccess ||
         cp(g->d_blocks, blocks.data(), sizeof(wb::CellBlock) * blocks.size()) != cudaSuccess)
         return bail(fail(WB_ECUDA, "table upload failed: %s", cudaGetErrorString(cudaGetLastError())));
@@ -645,10 +716,10 @@ int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
     double* db = b_out ? g->d_io + 8 * N : nullptr;
     if (g->precision == WB_FP64)
         WB_CK(wb::launch_export<double>(static_cast<const double*>(g->un), dU, db, g->d_blocks,
-                                        g->d_patches, N, g->nblocks, g->stream));
+                                        g->d_patches, g->d_links, N, g->nblocks, g->stream));
     else
         WB_CK(wb::launch_export<float>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
-                                       g->d_patches, N, g->nblocks, g->stream));
+                                       g->d_patches, g->d_links, N, g->nblocks, g->stream));
     if (U_out)
         WB_CK(cudaMemcpyAsync(U_out, dU, sizeof(double) * 8 * N, cudaMemcpyDeviceToHost, g->stream));
     if (b_out)
@@ -672,6 +743,7 @@ int wb_harvest(wb_grid* g, int axis, const long long* cells, long long n, const 
         return fail(WB_EINVAL, "harvest: null argument or no samples");
     if (g->precision != WB_FP64) return fail(WB_EINVAL, "harvest: needs an FP64 grid");
     if (axis < 0 || axis > 2) return fail(WB_EINVAL, "harvest: axis must be 0, 1 or 2");
+    if (g->d_links) return fail(WB_EINVAL, "harvest: needs a periodic patch 0 (grid has links)");
     const wb::PatchDev& P = g->h_patches[0];
     const long long np = (long long)P.nx * P.ny * P.nz;
     for (long long t = 0; t < n; t++)

@@ -14,6 +14,41 @@ struct PatchDev {
     long long off;
 };
 
+// Cell addressing across patch boundaries.  Sec. 2.2 resolves each patch
+// with the ghost zones its neighbours provide; here a patch reads its
+// neighbours' cells in place.  links == nullptr: every patch is periodic on
+// itself.  Otherwise links[27 p + 9 (oz+1) + 3 (oy+1) + (ox+1)] is the patch
+// that continues patch p in direction (ox, oy, oz) in {-1, 0, 1}^3; the host
+// has checked that linked patches agree in the extents they share and are at
+// least 3 cells deep wherever a stencil crosses into them.  (i, j, k) may lie
+// up to 3 cells outside patch p; the result is the flat cell index.
+__device__ __forceinline__ int wrap_cell(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ long long locate(const PatchDev* __restrict__ patches,
+                                            const int* __restrict__ links, int p,
+                                            const PatchDev& P, int i, int j, int k) {
+    const int ox = i < 0 ? -1 : (i >= P.nx ? 1 : 0);
+    const int oy = j < 0 ? -1 : (j >= P.ny ? 1 : 0);
+    const int oz = k < 0 ? -1 : (k >= P.nz ? 1 : 0);
+    if ((ox | oy | oz) == 0) return P.off + ((long long)k * P.ny + j) * P.nx + i;
+    if (links == nullptr)
+        return P.off + ((long long)wrap_cell(k, P.nz) * P.ny + wrap_cell(j, P.ny)) * P.nx +
+               wrap_cell(i, P.nx);
+    const int q = links[27 * p + 9 * (oz + 1) + 3 * (oy + 1) + (ox + 1)];
+    const PatchDev Q = patches[q];
+    i = ox < 0 ? i + Q.nx : (ox > 0 ? i - P.nx : i);
+    j = oy < 0 ? j + Q.ny : (oy > 0 ? j - P.ny : j);
+    k = oz < 0 ? k + Q.nz : (oz > 0 ? k - P.nz : k);
+    // a patch linked to itself along an axis shorter than the stencil reach
+    if (i < 0 || i >= Q.nx) i = wrap_cell(i, Q.nx);
+    if (j < 0 || j >= Q.ny) j = wrap_cell(j, Q.ny);
+    if (k < 0 || k >= Q.nz) k = wrap_cell(k, Q.nz);
+    return Q.off + ((long long)k * Q.ny + j) * Q.nx + i;
+}
+
 // Sweep tile: x = patch, y = start along the sweep axis, z = start along the
 // pencil axis, w = fixed third coordinate.
 using Tile = int4;
@@ -35,6 +70,7 @@ struct SweepArgs {
     T* __restrict__ er;            // cell -v x B (3 arrays) or nullptr
     const Tile* __restrict__ tiles;
     const PatchDev* __restrict__ patches;
+    const int* __restrict__ links = nullptr;   // patch links (see locate) or nullptr
     long long ncells;              // stride between arrays
     double gamma;
     int zweights = 0;              // 1: WENO-Z weights instead of Jiang-Shu
@@ -52,6 +88,7 @@ struct UpdateArgs {
     T* emf;                        // 3 arrays of edge EMFs (E_x, E_y, E_z)
     const CellBlock* __restrict__ blocks;
     const PatchDev* __restrict__ patches;
+    const int* __restrict__ links; // patch links (see locate) or nullptr
     const double* __restrict__ dt; // device scalar
     long long ncells;
     double idx, idy, idz;
@@ -91,7 +128,7 @@ cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, in
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
-                       long long ncells, int nblocks, double idx, double idy, double idz,
+                       const int* links, long long ncells, int nblocks, double idx, double idy, double idz,
                        double gamma, unsigned long long* smax_bits, unsigned int* flag,
                        cudaStream_t s);
 cudaError_t launch_set_dt(const unsigned long long* smax_bits, double cfl, double fixed_dt,
@@ -112,7 +149,7 @@ cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* bloc
                                cudaStream_t s);
 template <class T>
 cudaError_t launch_export(const T* state, double* U, double* b,
-                          const CellBlock* blocks, const PatchDev* patches,
+                          const CellBlock* blocks, const PatchDev* patches, const int* links,
                           long long ncells, int nblocks, cudaStream_t s);
 
 }  // namespace wb

@@ -8,8 +8,6 @@
 namespace wb {
 namespace {
 
-__device__ __forceinline__ int inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
-
 // dt rule: s = sum_d (|v_d| + c_f,d) / dx_d per cell, maximised over cells;
 // the fast speed along d uses B_d as the normal field.  The per-cell speed is
 // taken in the state's precision (FP32 in FP32 mode: FP64 division and square
@@ -18,8 +16,9 @@ __device__ __forceinline__ int inc(int i, int n) { return i + 1 == n ? 0 : i + 1
 template <class T>
 __global__ void __launch_bounds__(kCellBlock)
 cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
-           const PatchDev* __restrict__ patches, long long N, double idx, double idy,
-           double idz, double gamma, unsigned long long* smax_bits, unsigned int* flag) {
+           const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
+           double idx, double idy, double idz, double gamma, unsigned long long* smax_bits,
+           unsigned int* flag) {
     const CellBlock cb = blocks[blockIdx.x];
     const PatchDev P = patches[cb.x];
     const int local = cb.y + threadIdx.x;
@@ -31,9 +30,9 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
         const int j = rem / P.nx;
         const int i = rem - j * P.nx;
         const long long c = P.off + local;
-        const long long cx = c + (inc(i, P.nx) - i);
-        const long long cy = c + (long long)(inc(j, P.ny) - j) * P.nx;
-        const long long cz = c + (long long)(inc(k, P.nz) - k) * nxy;
+        const long long cx = locate(patches, links, cb.x, P, i + 1, j, k);
+        const long long cy = locate(patches, links, cb.x, P, i, j + 1, k);
+        const long long cz = locate(patches, links, cb.x, P, i, j, k + 1);
         const T g = T(gamma);
         const T rho = q[c];
         const T rinv = T(1) / rho;
@@ -181,7 +180,7 @@ template <class T>
 __global__ void __launch_bounds__(kCellBlock)
 export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restrict__ b,
               const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
-              long long N) {
+              const int* __restrict__ links, long long N) {
     const CellBlock cb = blocks[blockIdx.x];
     const PatchDev P = patches[cb.x];
     const int nxy = P.nx * P.ny;
@@ -193,9 +192,9 @@ export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restric
     const int j = rem / P.nx;
     const int i = rem - j * P.nx;
     const long long c = P.off + local;
-    const long long cx = c + (inc(i, P.nx) - i);
-    const long long cy = c + (long long)(inc(j, P.ny) - j) * P.nx;
-    const long long cz = c + (long long)(inc(k, P.nz) - k) * nxy;
+    const long long cx = locate(patches, links, cb.x, P, i + 1, j, k);
+    const long long cy = locate(patches, links, cb.x, P, i, j + 1, k);
+    const long long cz = locate(patches, links, cb.x, P, i, j, k + 1);
     if (U) {
         double* u = U + 8 * P.off + local;
         u[0] = double(q[c]);
@@ -244,12 +243,12 @@ cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* bloc
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
-                       long long ncells, int nblocks, double idx, double idy, double idz,
-                       double gamma, unsigned long long* smax_bits, unsigned int* flag,
-                       cudaStream_t s) {
+                       const int* links, long long ncells, int nblocks, double idx, double idy,
+                       double idz, double gamma, unsigned long long* smax_bits,
+                       unsigned int* flag, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    cfl_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, ncells, idx, idy, idz,
-                                                 gamma, smax_bits, flag);
+    cfl_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx, idy,
+                                                 idz, gamma, smax_bits, flag);
     return cudaGetLastError();
 }
 
@@ -279,21 +278,23 @@ cudaError_t launch_import(const double* U, const double* b, T* state, const Cell
 
 template <class T>
 cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock* blocks,
-                          const PatchDev* patches, long long ncells, int nblocks, cudaStream_t s) {
-    export_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, ncells);
+                          const PatchDev* patches, const int* links, long long ncells, int nblocks,
+                          cudaStream_t s) {
+    export_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
     return cudaGetLastError();
 }
 
 #define WB_INST(T)                                                                            \
-    template cudaError_t launch_cfl<T>(const T*, const CellBlock*, const PatchDev*, long long, \
-                                       int, double, double, double, double,                  \
+    template cudaError_t launch_cfl<T>(const T*, const CellBlock*, const PatchDev*, const int*, \
+                                       long long, int, double, double, double, double,       \
                                        unsigned long long*, unsigned int*, cudaStream_t);     \
     template cudaError_t launch_totals<T>(const T*, const PatchDev*, int, long long, double*, \
                                           int, double, double*, cudaStream_t);                \
     template cudaError_t launch_import<T>(const double*, const double*, T*, const CellBlock*, \
                                           const PatchDev*, long long, int, cudaStream_t);     \
     template cudaError_t launch_export<T>(const T*, double*, double*, const CellBlock*,       \
-                                          const PatchDev*, long long, int, cudaStream_t);     \
+                                          const PatchDev*, const int*, long long, int,        \
+                                          cudaStream_t);                                      \
     template cudaError_t launch_export_flux<T>(const T*, double*, const CellBlock*,           \
                                                const PatchDev*, long long, int, cudaStream_t);
 WB_INST(float)

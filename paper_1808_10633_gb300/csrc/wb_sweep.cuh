@@ -288,18 +288,17 @@ struct RawCell {
     T rho, mx, my, mz, E, bx0, bx1, by0, by1, bz0, bz1;
 };
 
+// (i, j, k) are coordinates of patch p and may lie outside it (the stencil
+// reaching into a neighbour, or round a periodic patch).
 template <class T>
-__device__ __forceinline__ void load_cell(const SweepArgs<T>& A, const PatchDev& P, int i, int j,
-                                          int k, RawCell<T>& r, long long& c) {
+__device__ __forceinline__ void load_cell(const SweepArgs<T>& A, int p, const PatchDev& P, int i,
+                                          int j, int k, RawCell<T>& r, long long& c) {
     const long long N = A.ncells;
     const T* __restrict__ q = A.src;
-    c = P.off + ((long long)k * P.ny + j) * P.nx + i;
-    const int ip = (i + 1 == P.nx) ? 0 : i + 1;
-    const int jp = (j + 1 == P.ny) ? 0 : j + 1;
-    const int kp = (k + 1 == P.nz) ? 0 : k + 1;
-    const long long cxp = c + (ip - i);
-    const long long cyp = c + (long long)(jp - j) * P.nx;
-    const long long czp = c + (long long)(kp - k) * P.nx * P.ny;
+    c = locate(A.patches, A.links, p, P, i, j, k);
+    const long long cxp = locate(A.patches, A.links, p, P, i + 1, j, k);
+    const long long cyp = locate(A.patches, A.links, p, P, i, j + 1, k);
+    const long long czp = locate(A.patches, A.links, p, P, i, j, k + 1);
     r.rho = q[c]; r.mx = q[N + c]; r.my = q[2 * N + c]; r.mz = q[3 * N + c]; r.E = q[4 * N + c];
     r.bx0 = q[5 * N + c]; r.bx1 = q[5 * N + cxp];
     r.by0 = q[6 * N + c]; r.by1 = q[6 * N + cyp];
@@ -648,12 +647,11 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
         rown[it] = raw_a >= tile.y && raw_a < tile.y + TA && raw_a < na;
         ridx[it] = AXIS == 0 ? tp * NS + s : s * TP + tp;
         if (rok[it]) {
-            const int ca = wrap(raw_a, na);
             int i, j, k;
-            if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
-            else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
-            else { i = cp; j = tile.w; k = ca; }
-            load_cell<T>(A, P, i, j, k, raw[it], rc[it]);
+            if (AXIS == 0) { i = raw_a; j = cp; k = tile.w; }
+            else if (AXIS == 1) { i = cp; j = raw_a; k = tile.w; }
+            else { i = cp; j = tile.w; k = raw_a; }
+            load_cell<T>(A, tile.x, P, i, j, k, raw[it], rc[it]);
         }
     }
 #pragma unroll
@@ -877,7 +875,7 @@ __device__ void harvest_one(const HarvestArgs<T>& H, long long t, T* sm, int nc,
         if (AXIS == 0) i = a; else if (AXIS == 1) j = a; else k = a;
         RawCell<T> r;
         long long c;
-        load_cell<T>(A, P, i, j, k, r, c);
+        load_cell<T>(A, 0, P, i, j, k, r, c);
         id[m] = base + m;
         derive_cell<T, AXIS>(A, r, c, sm, nc, id[m], false);
         const T p = sm[SP_P * nc + id[m]];

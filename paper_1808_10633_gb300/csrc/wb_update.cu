@@ -24,14 +24,16 @@
 namespace wb {
 namespace {
 
-__device__ __forceinline__ int dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
-__device__ __forceinline__ int inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
-
+// Cell (i, j, k) of patch p, where an index one step outside the patch
+// reaches the neighbouring patch (or wraps round a periodic patch).
 template <class T>
 struct Geo {
     const PatchDev P;
+    const PatchDev* __restrict__ patches;
+    const int* __restrict__ links;
+    int p;
     __device__ __forceinline__ long long at(int i, int j, int k) const {
-        return P.off + ((long long)k * P.ny + j) * P.nx + i;
+        return locate(patches, links, p, P, i, j, k);
     }
 };
 
@@ -43,7 +45,7 @@ __device__ __forceinline__ T emf_z(const UpdateArgs<T>& A, const Geo<T>& G, int 
     const long long N = A.ncells;
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fy = A.flux + 7 * N;
-    const int im = dec(i, G.P.nx), jm = dec(j, G.P.ny);
+    const int im = i - 1, jm = j - 1;
     const long long c = G.at(i, j, k), cjm = G.at(i, jm, k), cim = G.at(im, j, k);
     const T fsum = -Fx[5 * N + cjm] - Fx[5 * N + c] + Fy[6 * N + cim] + Fy[6 * N + c];
     if (A.emf_mode == 1) return T(0.25) * fsum;
@@ -58,7 +60,7 @@ __device__ __forceinline__ T emf_y(const UpdateArgs<T>& A, const Geo<T>& G, int 
     const long long N = A.ncells;
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fz = A.flux + 14 * N;
-    const int im = dec(i, G.P.nx), km = dec(k, G.P.nz);
+    const int im = i - 1, km = k - 1;
     const long long c = G.at(i, j, k), ckm = G.at(i, j, km), cim = G.at(im, j, k);
     const T fsum = Fx[6 * N + ckm] + Fx[6 * N + c] - Fz[5 * N + cim] - Fz[5 * N + c];
     if (A.emf_mode == 1) return T(0.25) * fsum;
@@ -73,7 +75,7 @@ __device__ __forceinline__ T emf_x(const UpdateArgs<T>& A, const Geo<T>& G, int 
     const long long N = A.ncells;
     const T* __restrict__ Fy = A.flux + 7 * N;
     const T* __restrict__ Fz = A.flux + 14 * N;
-    const int jm = dec(j, G.P.ny), km = dec(k, G.P.nz);
+    const int jm = j - 1, km = k - 1;
     const long long c = G.at(i, j, k), ckm = G.at(i, j, km), cjm = G.at(i, jm, k);
     const T fsum = -Fy[5 * N + ckm] - Fy[5 * N + c] + Fz[6 * N + cjm] + Fz[6 * N + c];
     if (A.emf_mode == 1) return T(0.25) * fsum;
@@ -109,7 +111,7 @@ __device__ __forceinline__ T combine(const UpdateArgs<T>& A, long long o, T L, T
 template <class T>
 __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T> G{A.patches[cb.x]};
+    const Geo<T> G{A.patches[cb.x], A.patches, A.links, cb.x};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) 
 template <class T>
 __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T> G{A.patches[cb.x]};
+    const Geo<T> G{A.patches[cb.x], A.patches, A.links, cb.x};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -137,9 +139,9 @@ __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<
     const int i = rem - j * G.P.nx;
     const long long N = A.ncells;
     const long long c = G.P.off + local;
-    const long long cx = G.at(inc(i, G.P.nx), j, k);
-    const long long cy = G.at(i, inc(j, G.P.ny), k);
-    const long long cz = G.at(i, j, inc(k, G.P.nz));
+    const long long cx = G.at(i + 1, j, k);
+    const long long cy = G.at(i, j + 1, k);
+    const long long cz = G.at(i, j, k + 1);
     const T dt = T(*A.dt);
     const T idx = T(A.idx), idy = T(A.idy), idz = T(A.idz);
     const T* __restrict__ Fx = A.flux;

@@ -43,6 +43,7 @@ class GridDesc(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("ghost", ctypes.c_int), ("precision", ctypes.c_int),
         ("integrator", ctypes.c_int), ("emf_mode", ctypes.c_int), ("weights", ctypes.c_int),
+        ("links", ctypes.POINTER(ctypes.c_int)),
     ]
 
 
@@ -116,18 +117,25 @@ class Grid:
     layout; b: faces (3, nz, ny, nx) or flat.  dims: list of (nx, ny, nz)."""
 
     def __init__(self, dims: Sequence[Sequence[int]], dx, dy, dz, U, b, gamma=5.0 / 3.0,
-                 precision="fp64", integrator="ssprk3", emf_mode=0, stream=None, weights="js"):
+                 precision="fp64", integrator="ssprk3", emf_mode=0, stream=None, weights="js",
+                 links=None):
         L = load()
         self._lib = L
         self.dims = [tuple(int(v) for v in d) for d in dims]
         self.ncells = sum(d[0] * d[1] * d[2] for d in self.dims)
         flat = np.array([v for d in self.dims for v in d], dtype=np.int32)
         self._dims = flat
+        lk = None
+        if links is not None:
+            lk = np.ascontiguousarray(links, dtype=np.int32).ravel()
+            assert lk.size == 27 * len(self.dims), (lk.size, len(self.dims))
+        self._links = lk
         desc = GridDesc(len(self.dims), flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                         float(dx), float(dy), float(dz), float(gamma), 3,
                         PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision,
                         INTEGRATORS.get(integrator, integrator) if isinstance(integrator, str) else integrator,
-                        int(emf_mode), {"js": 0, "z": 1}.get(weights, weights))
+                        int(emf_mode), {"js": 0, "z": 1}.get(weights, weights),
+                        lk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if lk is not None else None)
         self.precision = precision
         U = self._host(U, 8)
         b = self._host(b, 3)
@@ -141,6 +149,17 @@ class Grid:
             a = np.ascontiguousarray(a, dtype=np.float64)
             assert a.size == nf * self.ncells, (a.shape, nf, self.ncells)
         return a
+
+    @classmethod
+    def from_bricks(cls, st, cuts, **kw):
+        """The world state `st` split at `cuts` (x, y, z cut positions, each
+        starting at 0 and ending at the world's extent) into linked brick
+        patches (see bricks.py)."""
+        from . import bricks
+
+        U, b = bricks.split(st.U, np.stack([st.bx, st.by, st.bz]), cuts)
+        return cls(bricks.brick_dims(cuts), st.dx, st.dy, st.dz, U, b, gamma=st.gamma,
+                   links=bricks.brick_links(cuts), **kw)
 
     @classmethod
     def from_state(cls, st, **kw):
