@@ -227,6 +227,11 @@ def run_native(args, rank, world, local):
     if args.patches > 0:
         patches = run_patches(args, world)
 
+    # ---- the same world as linked bricks ------------------------------------
+    linked = None
+    if not args.no_linked:
+        linked = run_linked(args, st, world)
+
     # ---- 512^3 turbulence + blasts, sweep kernels only (config 3) -----------
     large = None
     if args.large_size > 0:
@@ -290,6 +295,7 @@ def run_native(args, rank, world, local):
         "learned": learned,
         "patches": patches,
         "large": large,
+        "linked": linked,
     })
     return out
 
@@ -335,6 +341,39 @@ def run_patches(args, world):
             "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
                             "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]},
             "generate_s": t_gen}
+
+
+def run_linked(args, st, world):
+    """The headline turbulence world cut into 4 x 4 x 4 uneven bricks that
+    read their neighbours' cells in place (FP32, same steps)."""
+    import torch
+
+    from paper_1808_10633_gb300 import wombat
+
+    n = args.size
+    cut = lambda f: [0] + [int(round(n * x)) for x in f] + [n]
+    cuts = (cut([0.22, 0.47, 0.74]), cut([0.27, 0.5, 0.77]), cut([0.24, 0.53, 0.76]))
+    g = wombat.Grid.from_bricks(st, cuts, precision="fp32")
+    for _ in range(args.warmup):
+        g.step_cfl(args.cfl, 1)
+    g.sync()
+    tot0, _, _ = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    tune = g.autotune()
+    for _ in range(2):
+        g.step_cfl(args.cfl, 1)
+    g.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    tot, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    barrier(world)
+    secs = max_over_ranks(tot / 1e3, world)
+    g.close()
+    return {"workload": f"turbulence {n}^3 as 64 linked bricks (cuts {cuts}), FP32",
+            "value": world * n ** 3 * args.steps / secs, "unit": UNIT,
+            "ms_per_step": secs * 1e3 / args.steps, "ms_per_step_cost_model_tiles": tot0 / args.steps,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
+                            "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]}}
 
 
 def run_large(args, world):
@@ -511,6 +550,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-weights leg")
+    ap.add_argument("--no-linked", action="store_true", help="skip the linked-bricks leg")
     ap.add_argument("--large-size", type=int, default=512,
                     help="edge of the turbulence + blasts leg timed on its sweeps (0: skip)")
     ap.add_argument("--large-steps", type=int, default=10)

@@ -13,7 +13,20 @@ namespace {
 // taken in the state's precision (FP32 in FP32 mode: FP64 division and square
 // root run at a small fraction of the FP32 rate on this GPU); the maximum is
 // reduced in FP64, which is exact.
-template <class T>
+// Upper neighbour of cell (i, j, k) of patch p along each axis: the wrap
+// round a periodic patch, or the link table's neighbour.
+template <bool LINKED>
+__device__ __forceinline__ long long upper(const PatchDev* __restrict__ patches,
+                                           const int* __restrict__ links, int p, const PatchDev& P,
+                                           int i, int j, int k) {
+    if constexpr (LINKED) return locate(patches, links, p, P, i, j, k);
+    i = i == P.nx ? 0 : i;
+    j = j == P.ny ? 0 : j;
+    k = k == P.nz ? 0 : k;
+    return P.off + ((long long)k * P.ny + j) * P.nx + i;
+}
+
+template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock)
 cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
            const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
@@ -30,9 +43,9 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
         const int j = rem / P.nx;
         const int i = rem - j * P.nx;
         const long long c = P.off + local;
-        const long long cx = locate(patches, links, cb.x, P, i + 1, j, k);
-        const long long cy = locate(patches, links, cb.x, P, i, j + 1, k);
-        const long long cz = locate(patches, links, cb.x, P, i, j, k + 1);
+        const long long cx = upper<LINKED>(patches, links, cb.x, P, i + 1, j, k);
+        const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
+        const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
         const T g = T(gamma);
         const T rho = q[c];
         const T rinv = T(1) / rho;
@@ -176,7 +189,7 @@ import_kernel(const double* __restrict__ U, const double* __restrict__ b, T* __r
     q[7 * N + c] = T(bb[2 * np]);
 }
 
-template <class T>
+template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock)
 export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restrict__ b,
               const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
@@ -192,9 +205,9 @@ export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restric
     const int j = rem / P.nx;
     const int i = rem - j * P.nx;
     const long long c = P.off + local;
-    const long long cx = locate(patches, links, cb.x, P, i + 1, j, k);
-    const long long cy = locate(patches, links, cb.x, P, i, j + 1, k);
-    const long long cz = locate(patches, links, cb.x, P, i, j, k + 1);
+    const long long cx = upper<LINKED>(patches, links, cb.x, P, i + 1, j, k);
+    const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
+    const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
     if (U) {
         double* u = U + 8 * P.off + local;
         u[0] = double(q[c]);
@@ -247,8 +260,12 @@ cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* 
                        double idz, double gamma, unsigned long long* smax_bits,
                        unsigned int* flag, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    cfl_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx, idy,
-                                                 idz, gamma, smax_bits, flag);
+    if (links)
+        cfl_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx,
+                                                           idy, idz, gamma, smax_bits, flag);
+    else
+        cfl_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx,
+                                                            idy, idz, gamma, smax_bits, flag);
     return cudaGetLastError();
 }
 
@@ -280,7 +297,10 @@ template <class T>
 cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock* blocks,
                           const PatchDev* patches, const int* links, long long ncells, int nblocks,
                           cudaStream_t s) {
-    export_kernel<T><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
+    if (links)
+        export_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
+    else
+        export_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
     return cudaGetLastError();
 }
 

@@ -288,22 +288,41 @@ struct RawCell {
     T rho, mx, my, mz, E, bx0, bx1, by0, by1, bz0, bz1;
 };
 
-// (i, j, k) are coordinates of patch p and may lie outside it (the stencil
-// reaching into a neighbour, or round a periodic patch).
+// Loads of one staged cell: the cell values and its three upper faces.
 template <class T>
-__device__ __forceinline__ void load_cell(const SweepArgs<T>& A, int p, const PatchDev& P, int i,
-                                          int j, int k, RawCell<T>& r, long long& c) {
+__device__ __forceinline__ void load_cell_at(const SweepArgs<T>& A, long long c, long long cxp,
+                                             long long cyp, long long czp, RawCell<T>& r) {
     const long long N = A.ncells;
     const T* __restrict__ q = A.src;
-    c = locate(A.patches, A.links, p, P, i, j, k);
-    const long long cxp = locate(A.patches, A.links, p, P, i + 1, j, k);
-    const long long cyp = locate(A.patches, A.links, p, P, i, j + 1, k);
-    const long long czp = locate(A.patches, A.links, p, P, i, j, k + 1);
     r.rho = q[c]; r.mx = q[N + c]; r.my = q[2 * N + c]; r.mz = q[3 * N + c]; r.E = q[4 * N + c];
     r.bx0 = q[5 * N + c]; r.bx1 = q[5 * N + cxp];
     r.by0 = q[6 * N + c]; r.by1 = q[6 * N + cyp];
     r.bz0 = q[7 * N + c]; r.bz1 = q[7 * N + czp];
 }
+
+// Cell (i, j, k) of a periodic patch P, all three indices inside it.
+template <class T>
+__device__ __forceinline__ void load_cell(const SweepArgs<T>& A, const PatchDev& P, int i, int j,
+                                          int k, RawCell<T>& r, long long& c) {
+    c = P.off + ((long long)k * P.ny + j) * P.nx + i;
+    const int ip = (i + 1 == P.nx) ? 0 : i + 1;
+    const int jp = (j + 1 == P.ny) ? 0 : j + 1;
+    const int kp = (k + 1 == P.nz) ? 0 : k + 1;
+    load_cell_at(A, c, c + (ip - i), c + (long long)(jp - j) * P.nx,
+                 c + (long long)(kp - k) * P.nx * P.ny, r);
+}
+
+// (i, j, k) are coordinates of patch p of a linked grid and may lie outside
+// it (the stencil reaching into a neighbour).
+template <class T>
+__device__ __forceinline__ void load_cell_linked(const SweepArgs<T>& A, int p, const PatchDev& P,
+                                                 int i, int j, int k, RawCell<T>& r, long long& c) {
+    c = locate(A.patches, A.links, p, P, i, j, k);
+    load_cell_at(A, c, locate(A.patches, A.links, p, P, i + 1, j, k),
+                 locate(A.patches, A.links, p, P, i, j + 1, k),
+                 locate(A.patches, A.links, p, P, i, j, k + 1), r);
+}
+
 
 template <class T, int AXIS>
 __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell<T>& r, long long c,
@@ -619,18 +638,22 @@ __host__ __device__ constexpr int max_nc(int axis) {
 }
 
 // One tile: stage the TA+5 cells of each of the TP pencils, then one thread
-// per interface.
-template <class T, int AXIS, int TA, int NCMAX, bool Z>
+// per interface.  TA_CT > 0 fixes the shape at compile time; TA_CT = 0 takes
+// it from ta_rt (a power of two), so that one body, and one register
+// allocation, serves every shape of a persistent launch.
+template <class T, int AXIS, int TA_CT, int NCMAX, bool Z>
 __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& tile, const PatchDev& P,
-                                          T* __restrict__ sm, int tid) {
-    constexpr int TP = 256 / TA;
-    constexpr int NS = TA + 5;
-    constexpr int NC = NS * TP;
+                                          T* __restrict__ sm, int tid, int ta_rt = 0) {
+    const int TA = TA_CT > 0 ? TA_CT : ta_rt;
+    const int lg_ta = TA_CT > 0 ? __builtin_ctz(TA_CT) : __ffs(ta_rt) - 1;
+    const int TP = 256 >> lg_ta;
+    const int NS = TA + 5;
+    const int NC = NS * TP;
     const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
     const int np = AXIS == 0 ? P.ny : P.nx;
 
     // staging: cells tile.y-3 .. tile.y+TA+1 along the axis, TP pencils
-    constexpr int NIT = (NC + 255) / 256;
+    constexpr int NIT = ((TA_CT > 0 ? (TA_CT + 5) * (256 / (TA_CT > 0 ? TA_CT : 1)) : NCMAX) + 255) / 256;
     RawCell<T> raw[NIT];
     long long rc[NIT];
     int ridx[NIT];
@@ -647,11 +670,13 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
         rown[it] = raw_a >= tile.y && raw_a < tile.y + TA && raw_a < na;
         ridx[it] = AXIS == 0 ? tp * NS + s : s * TP + tp;
         if (rok[it]) {
+            const int ca = A.links ? raw_a : wrap(raw_a, na);
             int i, j, k;
-            if (AXIS == 0) { i = raw_a; j = cp; k = tile.w; }
-            else if (AXIS == 1) { i = cp; j = raw_a; k = tile.w; }
-            else { i = cp; j = tile.w; k = raw_a; }
-            load_cell<T>(A, tile.x, P, i, j, k, raw[it], rc[it]);
+            if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
+            else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
+            else { i = cp; j = tile.w; k = ca; }
+            if (A.links) load_cell_linked<T>(A, tile.x, P, i, j, k, raw[it], rc[it]);
+            else load_cell<T>(A, P, i, j, k, raw[it], rc[it]);
         }
     }
 #pragma unroll
@@ -660,8 +685,8 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     __syncthreads();
 
     int ta, tp;
-    if (AXIS == 0) { ta = tid % TA; tp = tid / TA; }
-    else { tp = tid % TP; ta = tid / TP; }
+    if (AXIS == 0) { ta = tid & (TA - 1); tp = tid >> lg_ta; }
+    else { tp = tid & (TP - 1); ta = tid >> (8 - lg_ta); }
     const int ia = tile.y + ta, ip = tile.z + tp;
     if (ia >= na || ip >= np) return;
     int id[6];
@@ -694,8 +719,8 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
 }
 
 // Persistent sweep: a grid of (SMs x resident blocks) strides over the tile
-// table; each tile is dispatched to the body of its shape (a block-uniform
-// branch), so patches of uneven sizes share one launch.
+// table; each tile carries its shape, read by one body with the shape as a
+// block-uniform runtime value, so patches of uneven sizes share one launch.
 template <class T, int AXIS, bool Z>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
     constexpr int NCMAX = max_nc(AXIS);
@@ -707,9 +732,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         const int shape = (unsigned)tile.x >> 24;
         tile.x &= 0xffffff;
         const PatchDev P = A.patches[tile.x];
-        if (shape == 0) tile_body<T, AXIS, shape_ta(AXIS, 0), NCMAX, Z>(A, tile, P, sm, tid);
-        else if (shape == 1) tile_body<T, AXIS, shape_ta(AXIS, 1), NCMAX, Z>(A, tile, P, sm, tid);
-        else tile_body<T, AXIS, shape_ta(AXIS, 2), NCMAX, Z>(A, tile, P, sm, tid);
+        tile_body<T, AXIS, 0, NCMAX, Z>(A, tile, P, sm, tid, shape_ta(AXIS, shape));
         __syncthreads();
     }
 }
@@ -875,7 +898,7 @@ __device__ void harvest_one(const HarvestArgs<T>& H, long long t, T* sm, int nc,
         if (AXIS == 0) i = a; else if (AXIS == 1) j = a; else k = a;
         RawCell<T> r;
         long long c;
-        load_cell<T>(A, 0, P, i, j, k, r, c);
+        load_cell<T>(A, P, i, j, k, r, c);
         id[m] = base + m;
         derive_cell<T, AXIS>(A, r, c, sm, nc, id[m], false);
         const T p = sm[SP_P * nc + id[m]];

@@ -232,11 +232,13 @@ __global__ void __launch_bounds__(256, 1) sweep_learned_kernel(const SweepArgs<f
         rown[it] = raw_a >= tile.y && raw_a < tile.y + TA && raw_a < na;
         ridx[it] = AXIS == 0 ? tp * NS + s : s * TP + tp;
         if (rok[it]) {
+            const int ca = A.links ? raw_a : wrap(raw_a, na);
             int i, j, k;
-            if (AXIS == 0) { i = raw_a; j = cp; k = tile.w; }
-            else if (AXIS == 1) { i = cp; j = raw_a; k = tile.w; }
-            else { i = cp; j = tile.w; k = raw_a; }
-            load_cell<T>(A, tile.x, P, i, j, k, raw[it], rc[it]);
+            if (AXIS == 0) { i = ca; j = cp; k = tile.w; }
+            else if (AXIS == 1) { i = cp; j = ca; k = tile.w; }
+            else { i = cp; j = tile.w; k = ca; }
+            if (A.links) load_cell_linked<T>(A, tile.x, P, i, j, k, raw[it], rc[it]);
+            else load_cell<T>(A, P, i, j, k, raw[it], rc[it]);
         }
     }
 #pragma unroll

@@ -25,23 +25,31 @@ namespace wb {
 namespace {
 
 // Cell (i, j, k) of patch p, where an index one step outside the patch
-// reaches the neighbouring patch (or wraps round a periodic patch).
-template <class T>
+// wraps round a periodic patch or, with LINKED, reaches the neighbouring
+// patch through the link table.
+template <class T, bool LINKED>
 struct Geo {
     const PatchDev P;
     const PatchDev* __restrict__ patches;
     const int* __restrict__ links;
     int p;
     __device__ __forceinline__ long long at(int i, int j, int k) const {
-        return locate(patches, links, p, P, i, j, k);
+        if constexpr (LINKED) {
+            return locate(patches, links, p, P, i, j, k);
+        } else {
+            i = i < 0 ? i + P.nx : (i >= P.nx ? i - P.nx : i);
+            j = j < 0 ? j + P.ny : (j >= P.ny ? j - P.ny : j);
+            k = k < 0 ? k + P.nz : (k >= P.nz ? k - P.nz : k);
+            return P.off + ((long long)k * P.ny + j) * P.nx + i;
+        }
     }
 };
 
 // Flux array layout per axis: rho, mx, my, mz, E, B_t1, B_t2 with
 // (t1, t2) = (y, z) for x faces, (z, x) for y faces, (x, y) for z faces.
 // EMF at the edge of cell-index (i, j, k): E_z at (i-1/2, j-1/2, k).
-template <class T>
-__device__ __forceinline__ T emf_z(const UpdateArgs<T>& A, const Geo<T>& G, int i, int j, int k) {
+template <class T, bool LINKED>
+__device__ __forceinline__ T emf_z(const UpdateArgs<T>& A, const Geo<T, LINKED>& G, int i, int j, int k) {
     const long long N = A.ncells;
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fy = A.flux + 7 * N;
@@ -55,8 +63,8 @@ __device__ __forceinline__ T emf_z(const UpdateArgs<T>& A, const Geo<T>& G, int 
 }
 
 // E_y at (i-1/2, j, k-1/2)
-template <class T>
-__device__ __forceinline__ T emf_y(const UpdateArgs<T>& A, const Geo<T>& G, int i, int j, int k) {
+template <class T, bool LINKED>
+__device__ __forceinline__ T emf_y(const UpdateArgs<T>& A, const Geo<T, LINKED>& G, int i, int j, int k) {
     const long long N = A.ncells;
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fz = A.flux + 14 * N;
@@ -70,8 +78,8 @@ __device__ __forceinline__ T emf_y(const UpdateArgs<T>& A, const Geo<T>& G, int 
 }
 
 // E_x at (i, j-1/2, k-1/2)
-template <class T>
-__device__ __forceinline__ T emf_x(const UpdateArgs<T>& A, const Geo<T>& G, int i, int j, int k) {
+template <class T, bool LINKED>
+__device__ __forceinline__ T emf_x(const UpdateArgs<T>& A, const Geo<T, LINKED>& G, int i, int j, int k) {
     const long long N = A.ncells;
     const T* __restrict__ Fy = A.flux + 7 * N;
     const T* __restrict__ Fz = A.flux + 14 * N;
@@ -108,10 +116,10 @@ __device__ __forceinline__ T combine(const UpdateArgs<T>& A, long long o, T L, T
     return A.acc[o] + dt6 * L;
 }
 
-template <class T>
+template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T> G{A.patches[cb.x], A.patches, A.links, cb.x};
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -126,10 +134,10 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) 
     A.emf[2 * N + c] = emf_z(A, G, i, j, k);
 }
 
-template <class T>
+template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T> G{A.patches[cb.x], A.patches, A.links, cb.x};
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -176,14 +184,16 @@ __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<
 template <class T>
 cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    emf_kernel<T><<<nblocks, kCellBlock, 0, s>>>(a);
+    if (a.links) emf_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(a);
+    else emf_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    update_kernel<T><<<nblocks, kCellBlock, 0, s>>>(a);
+    if (a.links) update_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(a);
+    else update_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
