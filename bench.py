@@ -33,15 +33,29 @@ if ROOT not in sys.path:
 
 METRIC = "zone-updates/s per RK step at 256^3 (FP32/learned vs FP64) at stated L1 error"
 UNIT = "zone-updates/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-FP64_FMA_PER_SM_PER_CLK = None   # measured (wb_alu_peak), see the design doc
 
 # Algorithmic FP operations of one interface of the sweep kernel (one
 # direction, one stage) and of one staged cell, counted from the kernel's
-# formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1); see the design doc.
+# formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1).
 SWEEP_FLOPS_PER_INTERFACE = 2040
 SWEEP_FLOPS_PER_STAGED_CELL = 80
+
+# DRAM bytes (read + write) per launch of the FP32 sweep kernels, from one
+# ncu capture of the 128^3 turbulence case (profiles/sweep_kernel_fixed_fp32_
+# turbulence128.md), scaled by the interface count; valid only while the
+# sweep sources hash to SWEEP_TRAFFIC_SOURCES.
+SWEEP_TRAFFIC_128 = {"sweep_x": 120.82e6, "sweep_y": 99.26e6, "sweep_z": 99.21e6}
+SWEEP_TRAFFIC_SOURCES = "4416d01e81e17b03"
+
+
+def sweep_sources_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("wb_sweep.cuh", "wb_sweep_f32.cu", "wb_internal.h"):
+        with open(os.path.join(ROOT, "paper_1808_10633_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def dist_env():
@@ -192,9 +206,16 @@ def run_native(args, rank, world, local):
         iface, staged = sweep_units(n)
         flops = iface * SWEEP_FLOPS_PER_INTERFACE + staged[cls] * SWEEP_FLOPS_PER_STAGED_CELL
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        return {"kernel": f"sweep_kernel<{label},{'xyz'[('sweep_x','sweep_y','sweep_z').index(cls)]}>",
+        traffic = None
+        if label == "float" and sweep_sources_hash() == SWEEP_TRAFFIC_SOURCES:
+            traffic = SWEEP_TRAFFIC_128[cls] * (n / 128) ** 3
+        return {"kernel": f"sweep_kernel_fixed<{label},{'xyz'[('sweep_x','sweep_y','sweep_z').index(cls)]}>",
                 "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
+                "traffic_note": None if traffic is None else
+                "ncu dram read+write of the 128^3 case scaled by interfaces (bytes per launch)",
+                "algorithmic_bytes_per_launch": iface * 4 * (8 + 7 + (3 if cls == "sweep_x" else 0))
+                * (1 if label == "float" else 2),
                 "flops_per_launch": flops, "ms_per_launch": round(per_launch_ms, 4),
                 "peak_source": "measured FMA throughput (wb_alu_peak) on this GPU"}
 
@@ -558,7 +579,8 @@ def main():
                     help="patch count of the batched-patch leg (0: skip)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out-dir", default=os.environ.get("WB_BENCH_OUT"),
+                    help="directory for the clock samples (CSV); none by default")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -28,54 +28,59 @@ __device__ __forceinline__ long long upper(const PatchDev* __restrict__ patches,
 
 template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock)
-cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks,
+cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nblocks,
            const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
            double idx, double idy, double idz, double gamma, unsigned long long* smax_bits,
            unsigned int* flag) {
-    const CellBlock cb = blocks[blockIdx.x];
-    const PatchDev P = patches[cb.x];
-    const int local = cb.y + threadIdx.x;
-    const int nxy = P.nx * P.ny;
     double s = 0.0;
-    if (local < nxy * P.nz) {
-        const int k = local / nxy;
-        const int rem = local - k * nxy;
-        const int j = rem / P.nx;
-        const int i = rem - j * P.nx;
-        const long long c = P.off + local;
-        const long long cx = upper<LINKED>(patches, links, cb.x, P, i + 1, j, k);
-        const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
-        const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
-        const T g = T(gamma);
-        const T rho = q[c];
-        const T rinv = T(1) / rho;
-        const T v[3] = {q[N + c] * rinv, q[2 * N + c] * rinv, q[3 * N + c] * rinv};
-        const T B[3] = {T(0.5) * (q[5 * N + c] + q[5 * N + cx]),
-                        T(0.5) * (q[6 * N + c] + q[6 * N + cy]),
-                        T(0.5) * (q[7 * N + c] + q[7 * N + cz])};
-        const T bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-        const T kin = T(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        const T p = (g - T(1)) * (q[4 * N + c] - kin - T(0.5) * bb);
-        const T a2 = g * p * rinv;
-        const T b2 = bb * rinv;
-        const T sum = a2 + b2;
-        const T id[3] = {T(idx), T(idy), T(idz)};
-        T sp = T(0);
+    // grid-stride over the cell blocks: one atomic per resident block, not
+    // one per 256 cells (same-address atomics serialise in L2)
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const CellBlock cb = blocks[b];
+        const PatchDev P = patches[cb.x];
+        const int local = cb.y + threadIdx.x;
+        const int nxy = P.nx * P.ny;
+        if (local < nxy * P.nz) {
+            const int k = local / nxy;
+            const int rem = local - k * nxy;
+            const int j = rem / P.nx;
+            const int i = rem - j * P.nx;
+            const long long c = P.off + local;
+            const long long cx = upper<LINKED>(patches, links, cb.x, P, i + 1, j, k);
+            const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
+            const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
+            const T g = T(gamma);
+            const T rho = q[c];
+            const T rinv = T(1) / rho;
+            const T v[3] = {q[N + c] * rinv, q[2 * N + c] * rinv, q[3 * N + c] * rinv};
+            const T B[3] = {T(0.5) * (q[5 * N + c] + q[5 * N + cx]),
+                            T(0.5) * (q[6 * N + c] + q[6 * N + cy]),
+                            T(0.5) * (q[7 * N + c] + q[7 * N + cz])};
+            const T bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+            const T kin = T(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            const T p = (g - T(1)) * (q[4 * N + c] - kin - T(0.5) * bb);
+            const T a2 = g * p * rinv;
+            const T b2 = bb * rinv;
+            const T sum = a2 + b2;
+            const T id[3] = {T(idx), T(idy), T(idz)};
+            T sp = T(0);
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const T ca2 = B[d] * B[d] * rinv;
-            T disc = sum * sum - T(4) * a2 * ca2;
-            disc = disc > T(0) ? disc : T(0);
-            const T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
-            sp += (fabs(v[d]) + cf) * id[d];
-        }
-        s = double(sp);
-        unsigned int bad = 0;
-        if (!(s <= DBL_MAX)) bad |= 1u;              // NaN or Inf
-        if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
-        if (bad) {
-            atomicOr(flag, bad);
-            s = 0.0;
+            for (int d = 0; d < 3; d++) {
+                const T ca2 = B[d] * B[d] * rinv;
+                T disc = sum * sum - T(4) * a2 * ca2;
+                disc = disc > T(0) ? disc : T(0);
+                const T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
+                sp += (fabs(v[d]) + cf) * id[d];
+            }
+            double sc = double(sp);
+            unsigned int bad = 0;
+            if (!(sc <= DBL_MAX)) bad |= 1u;             // NaN or Inf
+            if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
+            if (bad) {
+                atomicOr(flag, bad);
+                sc = 0.0;
+            }
+            s = fmax(s, sc);
         }
     }
 #pragma unroll
@@ -260,12 +265,20 @@ cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* 
                        double idz, double gamma, unsigned long long* smax_bits,
                        unsigned int* flag, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = 8 * (nsm > 0 ? nsm : 152);      // one wave of 256-thread blocks
+    }
+    const int grid = nblocks < grid_cap ? nblocks : grid_cap;
     if (links)
-        cfl_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx,
-                                                           idy, idz, gamma, smax_bits, flag);
+        cfl_kernel<T, true><<<grid, kCellBlock, 0, s>>>(state, blocks, nblocks, patches, links, ncells,
+                                                        idx, idy, idz, gamma, smax_bits, flag);
     else
-        cfl_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(state, blocks, patches, links, ncells, idx,
-                                                            idy, idz, gamma, smax_bits, flag);
+        cfl_kernel<T, false><<<grid, kCellBlock, 0, s>>>(state, blocks, nblocks, patches, links, ncells,
+                                                         idx, idy, idz, gamma, smax_bits, flag);
     return cudaGetLastError();
 }
 
