@@ -96,6 +96,8 @@ struct wb_grid {
     int ntiles[3] = {0, 0, 0};
     wb::CellBlock* d_blocks = nullptr;
     int nblocks = 0;
+    wb::CellBlock* d_vblocks = nullptr;   // vector blocks of the per-cell kernels (periodic grids)
+    int nvblocks = 0;
     double* d_scalars = nullptr;          // dt, time
     unsigned long long* d_smax = nullptr;
     unsigned int* d_flag = nullptr;
@@ -157,6 +159,8 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
         u.blocks = g->d_blocks;
         u.patches = g->d_patches;
         u.links = g->d_links;
+        u.vblocks = g->d_vblocks;
+        u.nvblocks = g->nvblocks;
         u.dt = g->d_scalars;
         u.ncells = N;
         u.idx = 1.0 / g->dx;
@@ -290,7 +294,7 @@ void release(wb_grid* g) {
     if (g->graph) cudaGraphExecDestroy(g->graph);
     void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_patches, g->d_links,
                     g->d_tiles[0],
-                    g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_scalars, g->d_smax,
+                    g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_vblocks, g->d_scalars, g->d_smax,
                     g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -566,6 +570,21 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
         g->tile_uniform[a] = tiles_uniform(tiles[a]);
     }
     g->nblocks = (int)blocks.size();
+    // vector blocks: periodic patches whose x extent is a multiple of the width
+    std::vector<wb::CellBlock> vblocks;
+    {
+        const int V = wb::update_vector_width(g->precision == WB_FP64);
+        bool ok = d->links == nullptr;
+        for (const wb::PatchDev& P : g->h_patches) ok = ok && P.nx % V == 0;
+        if (ok)
+            for (int p = 0; p < g->npatch; p++) {
+                const wb::PatchDev& P = g->h_patches[p];
+                const long long np = (long long)P.nx * P.ny * P.nz;
+                for (long long c = 0; c < np; c += (long long)wb::kCellBlock * V)
+                    vblocks.push_back(wb::CellBlock{p, (int)c});
+            }
+        g->nvblocks = (int)vblocks.size();
+    }
 
     const size_t T = g->tsize;
     const long long N = g->N;
@@ -580,6 +599,8 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     for (int a = 0; a < 3; a++)
         if ((rc = dmalloc(g, &g->d_tiles[a], sizeof(wb::Tile) * tiles[a].size()))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_blocks, sizeof(wb::CellBlock) * blocks.size()))) return bail(rc);
+    if (!vblocks.empty() &&
+        (rc = dmalloc(g, &g->d_vblocks, sizeof(wb::CellBlock) * vblocks.size()))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_scalars, sizeof(double) * 2))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_smax, sizeof(unsigned long long)))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_flag, sizeof(unsigned int)))) return bail(rc);
@@ -594,7 +615,9 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (d->links && cp(g->d_links, d->links, sizeof(int) * 27 * (size_t)g->npatch) != cudaSuccess)
         return bail(fail(WB_ECUDA, "link upload failed"));
     if (cp(g->d_patches, g->h_patches.data(), sizeof(wb::PatchDev) * g->npatch) != cudaSuccess ||
-        cp(g->d_blocks, blocks.data(), sizeof(wb::CellBlock) * blocks.size()) != cudaSuccess)
+        cp(g->d_blocks, blocks.data(), sizeof(wb::CellBlock) * blocks.size()) != cudaSuccess ||
+        (!vblocks.empty() &&
+         cp(g->d_vblocks, vblocks.data(), sizeof(wb::CellBlock) * vblocks.size()) != cudaSuccess))
         return bail(fail(WB_ECUDA, "table upload failed: %s", cudaGetErrorString(cudaGetLastError())));
     for (int a = 0; a < 3; a++)
         if (cp(g->d_tiles[a], tiles[a].data(), sizeof(wb::Tile) * tiles[a].size()) != cudaSuccess)

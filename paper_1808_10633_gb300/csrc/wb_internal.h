@@ -87,6 +87,8 @@ struct UpdateArgs {
     const T* __restrict__ er;      // 3 arrays (emf_mode 0) or nullptr
     T* emf;                        // 3 arrays of edge EMFs (E_x, E_y, E_z)
     const CellBlock* __restrict__ blocks;
+    const CellBlock* __restrict__ vblocks;   // blocks of 256 vectors of cells along x, or nullptr
+    int nvblocks;
     const PatchDev* __restrict__ patches;
     const int* __restrict__ links; // patch links (see locate) or nullptr
     const double* __restrict__ dt; // device scalar
@@ -114,6 +116,8 @@ template <class T>
 cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
 template <class T>
 cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);
+// Cells per thread of the vector forms of the EMF and update kernels (16 bytes).
+int update_vector_width(bool fp64);
 
 cudaError_t prepare_sweep_learned();
 cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles, const uint32_t* mlp,
