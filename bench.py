@@ -469,10 +469,12 @@ def run_learned(args, st, world, peak32):
     gl.sync()
     barrier(world)
     torch.cuda.synchronize()
+    gl.learned_stats(reset=True)
     tot, kms, kcnt = gl.step_profiled(args.cfl, args.steps, with_totals=True)
     barrier(world)
     secs = max_over_ranks(tot / 1e3, world)
     value = world * zones * args.steps / secs
+    fired, decisions = gl.learned_stats(reset=True)
     # MLP work: 14 evaluations (7 fields x 2 sides) of 2*(6*32+32*32+32*3) flops per interface
     mlp_flops = 14 * 2 * (6 * 32 + 32 * 32 + 32 * 3) * zones
     cls = max(("sweep_x", "sweep_y", "sweep_z"), key=lambda k: kms[k])
@@ -483,7 +485,8 @@ def run_learned(args, st, world, peak32):
            "train": {"records": int(rec.shape[0]), "unflagged": int((rec[:, 11] == 0).sum()),
                      "steps": 1500, "harvest_s": t_h, "train_s": t_t,
                      "loss_first": float(hist[:20].mean()), "loss_last": float(hist[-20:].mean())},
-           "sweep_mlp_tflops": mlp_flops / (ms_l * 1e-3) / 1e12}
+           "sweep_mlp_tflops": mlp_flops / (ms_l * 1e-3) / 1e12,
+           "detector_fire_rate": fired / max(decisions, 1), "weight_decisions": decisions}
     if args.l1_steps > 0:
         nst = max(1, args.l1_steps // 2)
         b5 = np.stack([st5.bx, st5.by, st5.bz])
@@ -501,6 +504,17 @@ def run_learned(args, st, world, peak32):
         Ul, _ = gl.get_state()
         res["error_vs_fp64_after_steps"] = nst
         res["l1_rel_vs_fp64"] = {"learned": _l1(Ul, U64), "fp32_js": _l1(U32, U64)}
+        # the plain turbulence workload (no blasts), same steps
+        b2 = np.stack([st.bx, st.by, st.bz])
+        g64 = wombat.Grid.from_state(st, precision="fp64")
+        dt2 = g64.cfl_dt(args.cfl)
+        g64.step(dt2, nst)
+        U64t, _ = g64.get_state()
+        g64.close()
+        gl.set_state(st.U, b2)
+        gl.step(dt2, nst)
+        Ult, _ = gl.get_state()
+        res["l1_rel_vs_fp64_turbulence"] = _l1(Ult, U64t)
     gl.close()
     return res
 

@@ -304,6 +304,14 @@ int wb_harvest(wb_grid *g, int axis, const long long *cells, long long n,
  * detector fires the Jiang-Shu weights are used.  Synchronises. */
 int wb_set_mlp(wb_grid *g, const float *params, double kappa, double pjump);
 
+/* Detector log of a WB_FP32_LEARNED grid: out[0] = weight decisions where a
+ * detector fired (Jiang-Shu weights used), out[1] = all weight decisions
+ * (7 characteristic fields x 2 sides per interface and sweep), counted on
+ * the device over every learned sweep since the grid was made or last
+ * reset; reset != 0 zeroes the counters afterwards.  Synchronises.
+ * Errors: WB_EINVAL (null argument, not a learned grid). */
+int wb_learned_stats(wb_grid *g, long long out[2], int reset);
+
 /* Library version string. */
 const char *wb_version(void);
 

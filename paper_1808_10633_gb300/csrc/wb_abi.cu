@@ -86,6 +86,7 @@ struct wb_grid {
     void* er = nullptr;
     void* emf = nullptr;
     uint32_t* d_mlp = nullptr;            // learned weights, fragment order
+    unsigned long long* d_lstats = nullptr;   // detector firings, decisions (learned grids)
     double kappa = 4.0, pjump = 0.5;
     int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
     int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
@@ -136,6 +137,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.gamma = g->gamma;
             a.zweights = g->weights;
             a.uniform_shape0 = g->tile_uniform[axis];
+            a.lstats = g->d_lstats;
             int rc = prof_begin(pf, g->stream);
             if (rc != WB_OK) return rc;
             if constexpr (sizeof(T) == 4) {
@@ -292,7 +294,8 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_patches, g->d_links,
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_lstats, g->d_patches,
+                    g->d_links,
                     g->d_tiles[0],
                     g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_vblocks, g->d_scalars, g->d_smax,
                     g->d_flag, g->d_partial, g->d_io};
@@ -606,6 +609,8 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if ((rc = dmalloc(g, &g->d_flag, sizeof(unsigned int)))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_partial, sizeof(double) * (kPartials * 8 + 8)))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_io, sizeof(double) * 11 * N))) return bail(rc);
+    if (g->precision == WB_FP32_LEARNED &&
+        (rc = dmalloc(g, &g->d_lstats, sizeof(unsigned long long) * 2))) return bail(rc);
     if (cudaMallocHost(reinterpret_cast<void**>(&g->h_small), 256) != cudaSuccess)
         return bail(fail(WB_ENOMEM, "pinned host allocation failed"));
 
@@ -622,7 +627,9 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     for (int a = 0; a < 3; a++)
         if (cp(g->d_tiles[a], tiles[a].data(), sizeof(wb::Tile) * tiles[a].size()) != cudaSuccess)
             return bail(fail(WB_ECUDA, "tile upload failed"));
-    if (cudaMemsetAsync(g->d_scalars, 0, sizeof(double) * 2, g->stream) != cudaSuccess ||
+    if ((g->d_lstats &&
+         cudaMemsetAsync(g->d_lstats, 0, sizeof(unsigned long long) * 2, g->stream) != cudaSuccess) ||
+        cudaMemsetAsync(g->d_scalars, 0, sizeof(double) * 2, g->stream) != cudaSuccess ||
         cudaMemsetAsync(g->d_flag, 0, sizeof(unsigned int), g->stream) != cudaSuccess ||
         cudaMemsetAsync(g->flux, 0, T * 3 * wb::kNFlux * N, g->stream) != cudaSuccess)
         return bail(fail(WB_ECUDA, "memset failed"));
@@ -861,6 +868,21 @@ int wb_autotune(wb_grid* g, double* ms_out) {
         g->graph = nullptr;
     }
     return WB_OK;
+}
+
+int wb_learned_stats(wb_grid* g, long long out[2], int reset) {
+    g_err.clear();
+    if (!g || !out) return fail(WB_EINVAL, "null argument");
+    if (!g->d_lstats) return fail(WB_EINVAL, "learned_stats: not a learned-weights grid");
+    WB_CK(cudaSetDevice(g->device));
+    unsigned long long h[2];
+    WB_CK(cudaMemcpyAsync(g->h_small, g->d_lstats, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    if (reset) WB_CK(cudaMemsetAsync(g->d_lstats, 0, sizeof(h), g->stream));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    std::memcpy(h, g->h_small, sizeof(h));
+    out[0] = (long long)h[0];
+    out[1] = (long long)h[1];
+    return check_flag(g);
 }
 
 int wb_sync(wb_grid* g) {

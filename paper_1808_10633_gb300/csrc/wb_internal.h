@@ -74,6 +74,7 @@ struct SweepArgs {
     long long ncells;              // stride between arrays
     double gamma;
     int zweights = 0;              // 1: WENO-Z weights instead of Jiang-Shu
+    unsigned long long* lstats = nullptr;   // learned sweep: detector firings, decisions
     int uniform_shape0 = 0;        // 1: every tile uses shape 0 (one tile per block)
 };
 

@@ -25,6 +25,10 @@
 namespace wb {
 namespace {
 
+#ifndef WB_LEARNED_MINB
+#define WB_LEARNED_MINB 2                        // resident 256-thread blocks per SM (128 registers)
+#endif
+
 constexpr int kMlpWords = 34;                    // per lane per field
 constexpr int kMlpSmemWords = WB_MLP_NFIELD * kMlpWords * 32;
 
@@ -142,6 +146,7 @@ struct LearnedWeights {
     int lane;
     bool pfire;               // pressure detector of this interface
     float kappa;
+    int nfire = 0;            // detector firings of this thread (fields x sides)
 
     __device__ __forceinline__ float corr(int s, const float (&w)[6], const float (&g)[6], float alpha) {
         const float ha = 0.5f * alpha;
@@ -177,6 +182,7 @@ struct LearnedWeights {
 #pragma unroll
             for (int k = 0; k < 4; k++) { a[k] = fabsf(D[k]); dmax = fmaxf(dmax, a[k]); dsum += a[k]; }
             fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f;
+            nfire += fire[side] ? 1 : 0;
         }
         __syncwarp();
         mlp_warp(W + s * kMlpWords * 32, in, om, lane);
@@ -195,7 +201,7 @@ struct LearnedWeights {
 };
 
 template <int AXIS>
-__global__ void __launch_bounds__(256, 1) sweep_learned_kernel(const SweepArgs<float> A,
+__global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(const SweepArgs<float> A,
                                                                const uint32_t* __restrict__ mlp,
                                                                float kappa, float pjump) {
     using T = float;
@@ -267,6 +273,16 @@ __global__ void __launch_bounds__(256, 1) sweep_learned_kernel(const SweepArgs<f
     T F[7];
     T* bp = sm + kNSlot * NC + tid;
     interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, lw, F);
+    if (A.lstats) {
+        // detector statistics: firings and decisions (7 fields x 2 sides) of
+        // the valid interfaces, one pair of atomics per warp
+        const unsigned nf = __reduce_add_sync(0xffffffffu, valid ? (unsigned)lw.nfire : 0u);
+        const unsigned nv = __reduce_add_sync(0xffffffffu, valid ? 14u : 0u);
+        if (lane == 0 && nv) {
+            atomicAdd(A.lstats, (unsigned long long)nf);
+            atomicAdd(A.lstats + 1, (unsigned long long)nv);
+        }
+    }
     if (!valid) return;
 
     int i, j, k;

@@ -26,7 +26,8 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune")
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune",
+           "wb_learned_stats")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -84,6 +85,7 @@ def load() -> ctypes.CDLL:
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
     L.wb_set_mlp.argtypes = [vp, vp, d, d]
     L.wb_autotune.argtypes = [vp, vp]
+    L.wb_learned_stats.argtypes = [vp, vp, i]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
@@ -236,6 +238,12 @@ class Grid:
         """Install the learned-weight networks (7 x 1379 floats)."""
         p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_NFIELD * MLP_NPARAM)
         _check(self._lib.wb_set_mlp(self._h, p.ctypes.data, float(kappa), float(pjump)))
+
+    def learned_stats(self, reset: bool = False):
+        """(detector firings, weight decisions) counted by the learned sweeps."""
+        out = (ctypes.c_longlong * 2)()
+        _check(self._lib.wb_learned_stats(self._h, out, int(bool(reset))))
+        return int(out[0]), int(out[1])
 
     def harvest(self, axis: int, cells, hU, hF, kappa: float = 4.0, pjump: float = 0.5):
         """Training records (n, 14, 12) for the lower faces of `cells` along axis."""

@@ -282,3 +282,23 @@ def test_learned_blasts_stay_positive(wb, trained):
     U = g.get_state_single()[0]
     g.close()
     assert dt > 0 and np.isfinite(U).all() and U[0].min() > 0
+
+
+def test_detector_log_counts_every_decision(wb):
+    """wb_learned_stats counts 7 fields x 2 sides per interface and sweep:
+    all of them when the detectors are forced on, none when forced off."""
+    from paper_1808_10633_gb300 import learned as Ln
+
+    st = I.turbulence(24, seed=34)
+    n = 24 ** 3 * 3 * 3 * 14               # interfaces x axes x stages x decisions
+    for kappa, pjump, fired in ((1e-30, 1e-30, n), (1e30, 1e30, 0)):
+        g = wb.Grid.from_state(st, precision="learned")
+        g.set_mlp(Ln.init_params(seed=2), kappa, pjump)
+        g.step(1e-3, 1)
+        assert g.learned_stats(reset=True) == (fired, n)
+        assert g.learned_stats() == (0, 0)
+        g.close()
+    g = wb.Grid.from_state(st, precision="fp32")
+    with pytest.raises(wb.WombatError):
+        g.learned_stats()
+    g.close()
