@@ -2,7 +2,10 @@
 
 nvcc compiles each translation unit of csrc/ in parallel (one -gencode,
 arch=compute_103a, code=sm_103a, -lineinfo) and links a shared library next
-to this file.  Objects go to _build/ (git-ignored).
+to this file.  Objects go to _build/ (git-ignored).  The "check" variant
+(libwombat_gb300_check.so, objects in _build_check/) is compiled with
+-DWB_BOUNDS_CHECK=1: the solver kernels test every index they form and
+report a bad one as WB_EINTERNAL instead of touching memory outside an array.
 """
 from __future__ import annotations
 
@@ -18,6 +21,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwombat_gb300.so")
+VARIANTS = {"release": (OBJ, LIB, []),
+            "check": (os.path.join(HERE, "_build_check"), os.path.join(HERE, "libwombat_gb300_check.so"),
+                      ["-DWB_BOUNDS_CHECK=1"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file extra flags: the FP32 sweep uses fast single-precision division
 # and square root (FP64 code in that file is unaffected)
@@ -50,23 +56,25 @@ def _deps():
         + [os.path.join(ROOT, "include", "wombat_gb300.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          variant: str = "release") -> str:
+    obj_dir, lib, vflags = VARIANTS[variant]
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *flags(verbose), *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc, *flags(verbose), *vflags, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -78,14 +86,15 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                variant="check" if "--check" in sys.argv else "release"))

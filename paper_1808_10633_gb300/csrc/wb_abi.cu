@@ -87,6 +87,7 @@ struct wb_grid {
     void* emf = nullptr;
     uint32_t* d_mlp = nullptr;            // learned weights, fragment order
     unsigned long long* d_lstats = nullptr;   // detector firings, decisions (learned grids)
+    int* d_queue = nullptr;               // per-axis tile counters of the persistent sweeps
     double kappa = 4.0, pjump = 0.5;
     int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
     int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
@@ -138,6 +139,8 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.zweights = g->weights;
             a.uniform_shape0 = g->tile_uniform[axis];
             a.lstats = g->d_lstats;
+            a.queue = g->d_queue + axis;
+            a.flag = g->d_flag;
             int rc = prof_begin(pf, g->stream);
             if (rc != WB_OK) return rc;
             if constexpr (sizeof(T) == 4) {
@@ -163,6 +166,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
         u.links = g->d_links;
         u.vblocks = g->d_vblocks;
         u.nvblocks = g->nvblocks;
+        u.flag = g->d_flag;
         u.dt = g->d_scalars;
         u.ncells = N;
         u.idx = 1.0 / g->dx;
@@ -269,6 +273,8 @@ int check_flag(wb_grid* g) {
     if (f) {
         WB_CK(cudaMemsetAsync(g->d_flag, 0, sizeof(unsigned int), g->stream));
         WB_CK(cudaStreamSynchronize(g->stream));
+        if (f & wb::kFlagBounds)
+            return fail(WB_EINTERNAL, "a kernel formed an index outside its array (bounds-checked build)");
         return fail(WB_ENONFINITE, "state holds %s",
                     (f & 1u) ? "NaN/Inf values" : "non-positive density or pressure");
     }
@@ -294,7 +300,8 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_lstats, g->d_patches,
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_lstats, g->d_queue,
+                    g->d_patches,
                     g->d_links,
                     g->d_tiles[0],
                     g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_vblocks, g->d_scalars, g->d_smax,
@@ -431,6 +438,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     a.gamma = g->gamma;
     a.zweights = g->weights;
     a.uniform_shape0 = g->tile_uniform[axis];
+    a.flag = g->d_flag;
     if constexpr (sizeof(T) == 4) {
         if (g->precision == WB_FP32_LEARNED) {
             if (!g->d_mlp) return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
@@ -464,6 +472,8 @@ int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, int unif
     a.gamma = g->gamma;
     a.zweights = g->weights;
     a.uniform_shape0 = uniform;
+    a.queue = g->d_queue + axis;
+    a.flag = g->d_flag;
     cudaEvent_t e0, e1;
     WB_CK(cudaEventCreate(&e0));
     WB_CK(cudaEventCreate(&e1));
@@ -611,6 +621,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if ((rc = dmalloc(g, &g->d_io, sizeof(double) * 11 * N))) return bail(rc);
     if (g->precision == WB_FP32_LEARNED &&
         (rc = dmalloc(g, &g->d_lstats, sizeof(unsigned long long) * 2))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_queue, sizeof(int) * 3))) return bail(rc);
     if (cudaMallocHost(reinterpret_cast<void**>(&g->h_small), 256) != cudaSuccess)
         return bail(fail(WB_ENOMEM, "pinned host allocation failed"));
 

@@ -49,6 +49,29 @@ __device__ __forceinline__ long long locate(const PatchDev* __restrict__ patches
     return Q.off + ((long long)k * Q.ny + j) * Q.nx + i;
 }
 
+// Bounds-checked builds (WB_BOUNDS_CHECK=1, the library's "check" variant):
+// each global or shared index the solver kernels form is tested against its
+// array; an index outside it sets kFlagBounds in the grid's status word and
+// is replaced by 0 (an in-range access), and the host reports the run as
+// WB_EINTERNAL.  In normal builds chk() is the identity.
+#ifndef WB_BOUNDS_CHECK
+#define WB_BOUNDS_CHECK 0
+#endif
+constexpr unsigned int kFlagBounds = 4u;
+
+__device__ __forceinline__ long long chk(long long i, long long n, unsigned int* flag) {
+#if WB_BOUNDS_CHECK
+    if (i < 0 || i >= n) {
+        if (flag) atomicOr(flag, kFlagBounds);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)flag;
+#endif
+    return i;
+}
+
 // Sweep tile: x = patch, y = start along the sweep axis, z = start along the
 // pencil axis, w = fixed third coordinate.
 using Tile = int4;
@@ -75,7 +98,9 @@ struct SweepArgs {
     double gamma;
     int zweights = 0;              // 1: WENO-Z weights instead of Jiang-Shu
     unsigned long long* lstats = nullptr;   // learned sweep: detector firings, decisions
+    int* queue = nullptr;          // persistent sweep: tile counter of this launch (or fixed stride)
     int uniform_shape0 = 0;        // 1: every tile uses shape 0 (one tile per block)
+    unsigned int* flag = nullptr;  // status word (bounds-checked builds)
 };
 
 template <class T>
@@ -98,6 +123,7 @@ struct UpdateArgs {
     int stage;                     // SSP-RK3: 0,1,2; RK4: 0..3
     int integrator;
     int emf_mode;
+    unsigned int* flag;            // status word (bounds-checked builds)
 };
 
 // Sets the calling thread's wb_last_error() message and returns `code`.

@@ -45,10 +45,10 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
             const int rem = local - k * nxy;
             const int j = rem / P.nx;
             const int i = rem - j * P.nx;
-            const long long c = P.off + local;
-            const long long cx = upper<LINKED>(patches, links, cb.x, P, i + 1, j, k);
-            const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
-            const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
+            const long long c = chk(P.off + local, N, flag);
+            const long long cx = chk(upper<LINKED>(patches, links, cb.x, P, i + 1, j, k), N, flag);
+            const long long cy = chk(upper<LINKED>(patches, links, cb.x, P, i, j + 1, k), N, flag);
+            const long long cz = chk(upper<LINKED>(patches, links, cb.x, P, i, j, k + 1), N, flag);
             const T g = T(gamma);
             const T rho = q[c];
             const T rinv = T(1) / rho;

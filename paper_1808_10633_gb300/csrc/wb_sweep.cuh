@@ -294,6 +294,10 @@ __device__ __forceinline__ void load_cell_at(const SweepArgs<T>& A, long long c,
                                              long long cyp, long long czp, RawCell<T>& r) {
     const long long N = A.ncells;
     const T* __restrict__ q = A.src;
+    c = chk(c, N, A.flag);
+    cxp = chk(cxp, N, A.flag);
+    cyp = chk(cyp, N, A.flag);
+    czp = chk(czp, N, A.flag);
     r.rho = q[c]; r.mx = q[N + c]; r.my = q[2 * N + c]; r.mz = q[3 * N + c]; r.E = q[4 * N + c];
     r.bx0 = q[5 * N + c]; r.bx1 = q[5 * N + cxp];
     r.by0 = q[6 * N + c]; r.by1 = q[6 * N + cyp];
@@ -328,6 +332,7 @@ template <class T, int AXIS>
 __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell<T>& r, long long c,
                                             T* __restrict__ sm, int nc, int idx, bool write_er) {
     const long long N = A.ncells;
+    idx = (int)chk(idx, nc, A.flag);
     const T rho = r.rho, E = r.E;
     const T Bx = T(0.5) * (r.bx0 + r.bx1);
     const T By = T(0.5) * (r.by0 + r.by1);
@@ -382,6 +387,7 @@ __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell
     sm[SP_P * nc + idx] = p;
     if (AXIS == 0 && write_er) {
         // -v x B in the global frame (x sweep: u = vx, v1 = vy, v2 = vz)
+        c = chk(c, N, A.flag);
         A.er[c] = v2 * b1 - v1 * b2;
         A.er[N + c] = u * b2 - v2 * bn;
         A.er[2 * N + c] = v1 * bn - u * b1;
@@ -691,7 +697,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     if (ia >= na || ip >= np) return;
     int id[6];
 #pragma unroll
-    for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
+    for (int m = 0; m < 6; m++) id[m] = (int)chk(AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp, NC, A.flag);
     T F[7];
     T* bp = sm + kNSlot * NCMAX + tid;      // this thread's back-projection slots
     JsWeights<T, Z> js;
@@ -702,8 +708,8 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     if (AXIS == 0) { i = ia; j = ip; k = tile.w; }
     else if (AXIS == 1) { i = ip; j = ia; k = tile.w; }
     else { i = ip; j = tile.w; k = ia; }
-    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
     const long long N = A.ncells;
+    const long long c = chk(P.off + ((long long)k * P.ny + j) * P.nx + i, N, A.flag);
     T* __restrict__ fo = A.flux;
     T fx, fy, fz;
     if (AXIS == 0) { fx = F[1]; fy = F[2]; fz = F[3]; }
@@ -727,13 +733,24 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.x;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __shared__ int next_tile;
+    // work queue: each block starts on tile blockIdx.x and then takes the next
+    // unclaimed tile from the launch's counter (zeroed before the launch), so
+    // uneven tiles balance across SMs; without a counter, a fixed stride
+    for (int t = blockIdx.x; t < ntiles;) {
         Tile tile = A.tiles[t];
         const int shape = (unsigned)tile.x >> 24;
         tile.x &= 0xffffff;
         const PatchDev P = A.patches[tile.x];
         tile_body<T, AXIS, 0, NCMAX, Z>(A, tile, P, sm, tid, shape_ta(AXIS, shape));
         __syncthreads();
+        if (A.queue) {
+            if (tid == 0) next_tile = gridDim.x + atomicAdd(A.queue, 1);
+            __syncthreads();
+            t = next_tile;
+        } else {
+            t += gridDim.x;
+        }
     }
 }
 
@@ -836,6 +853,10 @@ cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream
     }
     const int grid = PersistGrid<T>::g[axis] > 0 ? PersistGrid<T>::g[axis] : 152;
     const int nb = ntiles < grid ? ntiles : grid;
+    if (a.queue) {
+        const cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
     if (a.zweights) {
         if (axis == 0) sweep_kernel<T, 0, true><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
         else if (axis == 1) sweep_kernel<T, 1, true><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     const int tp = ip < np ? tp0 : 0;                      // stand-in stencil for idle lanes
     int id[6];
 #pragma unroll
-    for (int m = 0; m < 6; m++) id[m] = AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp;
+    for (int m = 0; m < 6; m++) id[m] = (int)chk(AXIS == 0 ? tp * NS + ta + m : (ta + m) * TP + tp, NC, A.flag);
     float pmin = sm[SP_P * NC + id[0]], pmax = pmin;
 #pragma unroll
     for (int m = 1; m < 6; m++) {
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     if (AXIS == 0) { i = ia; j = ip; k = tile.w; }
     else if (AXIS == 1) { i = ip; j = ia; k = tile.w; }
     else { i = ip; j = tile.w; k = ia; }
-    const long long c = P.off + ((long long)k * P.ny + j) * P.nx + i;
     const long long N = A.ncells;
+    const long long c = chk(P.off + ((long long)k * P.ny + j) * P.nx + i, N, A.flag);
     T* __restrict__ fo = A.flux;
     T fx, fy, fz;
     if (AXIS == 0) { fx = F[1]; fy = F[2]; fz = F[3]; }

@@ -97,14 +97,16 @@ struct Geo {
     const PatchDev* __restrict__ patches;
     const int* __restrict__ links;
     int p;
+    long long N;
+    unsigned int* flag;
     __device__ __forceinline__ long long at(int i, int j, int k) const {
         if constexpr (LINKED) {
-            return locate(patches, links, p, P, i, j, k);
+            return chk(locate(patches, links, p, P, i, j, k), N, flag);
         } else {
             i = i < 0 ? i + P.nx : (i >= P.nx ? i - P.nx : i);
             j = j < 0 ? j + P.ny : (j >= P.ny ? j - P.ny : j);
             k = k < 0 ? k + P.nz : (k >= P.nz ? k - P.nz : k);
-            return P.off + ((long long)k * P.ny + j) * P.nx + i;
+            return chk(P.off + ((long long)k * P.ny + j) * P.nx + i, N, flag);
         }
     }
 };
@@ -114,7 +116,7 @@ struct Geo {
 template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x};
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x, A.ncells, A.flag};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) 
     const int j = rem / G.P.nx;
     const int i = rem - j * G.P.nx;
     const long long N = A.ncells;
-    const long long c = G.P.off + local;
+    const long long c = chk(G.P.off + local, N, A.flag);
     const long long cim = G.at(i - 1, j, k), cjm = G.at(i, j - 1, k), ckm = G.at(i, j, k - 1);
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fy = A.flux + 7 * N;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) 
 template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
-    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x};
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x, A.ncells, A.flag};
     const int local = cb.y + threadIdx.x;
     const int nxy = G.P.nx * G.P.ny;
     if (local >= nxy * G.P.nz) return;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<
     const int j = rem / G.P.nx;
     const int i = rem - j * G.P.nx;
     const long long N = A.ncells;
-    const long long c = G.P.off + local;
+    const long long c = chk(G.P.off + local, N, A.flag);
     const long long cx = G.at(i + 1, j, k);
     const long long cy = G.at(i, j + 1, k);
     const long long cz = G.at(i, j, k + 1);
@@ -222,7 +224,8 @@ struct VRow {
 };
 
 template <int V>
-__device__ __forceinline__ bool vrow(const CellBlock& cb, const PatchDev& P, int tid, VRow& r) {
+__device__ __forceinline__ bool vrow(const CellBlock& cb, const PatchDev& P, int tid, VRow& r, long long N,
+                                     unsigned int* flag) {
     const int local = cb.y + tid * V;
     const int nxy = P.nx * P.ny;
     if (local >= nxy * P.nz) return false;
@@ -245,6 +248,19 @@ __device__ __forceinline__ bool vrow(const CellBlock& cb, const PatchDev& P, int
     r.cymzm = at(i, jm, km);
     r.cxmym = at(im, jm, k);
     r.cxmzm = at(im, j, km);
+#if WB_BOUNDS_CHECK
+    // every vector inside the arrays and aligned, every scalar neighbour inside
+    auto vec_ok = [&](long long a) { return a >= 0 && a + V <= N && a % V == 0; };
+    auto one_ok = [&](long long a) { return a >= 0 && a < N; };
+    if (!(vec_ok(r.c) && vec_ok(r.cym) && vec_ok(r.cyp) && vec_ok(r.czm) && vec_ok(r.czp) &&
+          vec_ok(r.cymzm) && one_ok(r.cxm) && one_ok(r.cxp) && one_ok(r.cxmym) && one_ok(r.cxmzm))) {
+        if (flag) atomicOr(flag, kFlagBounds);
+        return false;
+    }
+#else
+    (void)N;
+    (void)flag;
+#endif
     return true;
 }
 
@@ -254,7 +270,7 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel_vec(const UpdateArgs<T>
     const CellBlock cb = A.blocks[blockIdx.x];
     const PatchDev P = A.patches[cb.x];
     VRow r;
-    if (!vrow<V>(cb, P, threadIdx.x, r)) return;
+    if (!vrow<V>(cb, P, threadIdx.x, r, A.ncells, A.flag)) return;
     const long long N = A.ncells;
     const T* __restrict__ Fx = A.flux;
     const T* __restrict__ Fy = A.flux + 7 * N;
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(kCellBlock, 4) update_kernel_vec(const UpdateA
     const CellBlock cb = A.blocks[blockIdx.x];
     const PatchDev P = A.patches[cb.x];
     VRow r;
-    if (!vrow<V>(cb, P, threadIdx.x, r)) return;
+    if (!vrow<V>(cb, P, threadIdx.x, r, A.ncells, A.flag)) return;
     const long long N = A.ncells;
     const T dt = T(*A.dt);
     const T idx = T(A.idx), idy = T(A.idy), idz = T(A.idz);

@@ -14,7 +14,8 @@ from typing import Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwombat_gb300.so")
+# WB_LIBRARY selects another build of the library (e.g. the bounds-checked one)
+LIB_PATH = os.environ.get("WB_LIBRARY") or os.path.join(HERE, "libwombat_gb300.so")
 
 WB_OK, WB_EINVAL, WB_ECUDA, WB_ENOMEM, WB_ENONFINITE, WB_ETIMEOUT, WB_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
 WB_FP64, WB_FP32, WB_FP32_LEARNED = 0, 1, 2
