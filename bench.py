@@ -146,8 +146,8 @@ def sweep_units(n):
     """(interfaces, staged cells) per launch of each sweep kernel at n^3."""
     from paper_1808_10633_gb300 import wombat  # noqa: F401  (library must load)
     iface = n ** 3
-    # x: tiles of 32 interfaces x 8 pencils stage 37 cells per pencil;
-    # y, z: tiles of 16 x 16 stage 21 cells per pencil.
+    # x: tiles of 32 interfaces along the axis stage 37 cells per pencil;
+    # y, z: tiles of 16 along the axis stage 21 cells per pencil.
     staged = {"sweep_x": n ** 3 * 37 / 32, "sweep_y": n ** 3 * 21 / 16, "sweep_z": n ** 3 * 21 / 16}
     return iface, staged
 

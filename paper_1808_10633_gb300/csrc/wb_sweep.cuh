@@ -608,7 +608,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 }
 
 // ---- the kernel -------------------------------------------------------------
-// Tile shapes (interfaces along the axis x pencils, 256 threads) and the
+// Tile shapes (interfaces along the axis x pencils) and the
 // number of resident blocks per SM the FP32 register budget is shaped for.
 #ifndef WB_SWEEP_TA_X
 #define WB_SWEEP_TA_X 32
@@ -619,16 +619,24 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #ifndef WB_SWEEP_MINB_F32
 #define WB_SWEEP_MINB_F32 2
 #endif
+// threads (= interfaces) per block of the Jiang-Shu / WENO-Z sweeps; the
+// register budget per thread is kept when it changes (blocks per SM scale)
+#ifndef WB_SWEEP_NT
+#define WB_SWEEP_NT 128
+#endif
+constexpr int kSweepNT = WB_SWEEP_NT;
+constexpr int kSweepLgNT = kSweepNT == 512 ? 9 : (kSweepNT == 256 ? 8 : (kSweepNT == 128 ? 7 : 6));
+static_assert((1 << kSweepLgNT) == kSweepNT, "sweep block size must be 64, 128, 256 or 512");
 template <int AXIS> struct Shape;
 template <> struct Shape<0> { static constexpr int TA = WB_SWEEP_TA_X, TP = 256 / WB_SWEEP_TA_X; };
 template <> struct Shape<1> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256 / WB_SWEEP_TA_YZ; };
 template <> struct Shape<2> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256 / WB_SWEEP_TA_YZ; };
 
-template <class T> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB_F32; };
+template <class T> struct MinBlocks { static constexpr int value = 256 / kSweepNT > 1 ? 256 / kSweepNT : 1; };
+template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB_F32 * 256 / kSweepNT; };
 
 // Tile shapes a tile may use, per axis: TA interfaces along the axis times
-// TP = 256 / TA pencils.  Shape 0 is the default; the host picks a shape per
+// TP = kSweepNT / TA pencils.  Shape 0 is the default; the host picks a shape per
 // patch (fewest thread slots for the patch's sizes) and stores it in the top
 // byte of the tile's patch field.
 __host__ __device__ constexpr int shape_ta(int axis, int s) {
@@ -636,7 +644,7 @@ __host__ __device__ constexpr int shape_ta(int axis, int s) {
                      : (s == 0 ? WB_SWEEP_TA_YZ : (s == 1 ? 8 : 32));
 }
 constexpr int kNShape = 3;
-__host__ __device__ constexpr int nc_of(int ta) { return (ta + 5) * (256 / ta); }
+__host__ __device__ constexpr int nc_of(int ta) { return (ta + 5) * (kSweepNT / ta); }
 __host__ __device__ constexpr int max_nc(int axis) {
     return nc_of(shape_ta(axis, 0)) > nc_of(shape_ta(axis, 1))
                ? (nc_of(shape_ta(axis, 0)) > nc_of(shape_ta(axis, 2)) ? nc_of(shape_ta(axis, 0)) : nc_of(shape_ta(axis, 2)))
@@ -652,21 +660,22 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
                                           T* __restrict__ sm, int tid, int ta_rt = 0) {
     const int TA = TA_CT > 0 ? TA_CT : ta_rt;
     const int lg_ta = TA_CT > 0 ? __builtin_ctz(TA_CT) : __ffs(ta_rt) - 1;
-    const int TP = 256 >> lg_ta;
+    const int TP = kSweepNT >> lg_ta;
     const int NS = TA + 5;
     const int NC = NS * TP;
     const int na = AXIS == 0 ? P.nx : (AXIS == 1 ? P.ny : P.nz);
     const int np = AXIS == 0 ? P.ny : P.nx;
 
     // staging: cells tile.y-3 .. tile.y+TA+1 along the axis, TP pencils
-    constexpr int NIT = ((TA_CT > 0 ? (TA_CT + 5) * (256 / (TA_CT > 0 ? TA_CT : 1)) : NCMAX) + 255) / 256;
+    constexpr int NIT = ((TA_CT > 0 ? (TA_CT + 5) * (kSweepNT / (TA_CT > 0 ? TA_CT : 1)) : NCMAX) + kSweepNT - 1)
+                        / kSweepNT;
     RawCell<T> raw[NIT];
     long long rc[NIT];
     int ridx[NIT];
     bool rok[NIT], rown[NIT];
 #pragma unroll
     for (int it = 0; it < NIT; it++) {
-        const int e = tid + it * 256;
+        const int e = tid + it * kSweepNT;
         int s, tp;
         if (AXIS == 0) { tp = e / NS; s = e - tp * NS; }
         else { s = e / TP; tp = e - s * TP; }
@@ -692,7 +701,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
 
     int ta, tp;
     if (AXIS == 0) { ta = tid & (TA - 1); tp = tid >> lg_ta; }
-    else { tp = tid & (TP - 1); ta = tid >> (8 - lg_ta); }
+    else { tp = tid & (TP - 1); ta = tid >> (kSweepLgNT - lg_ta); }
     const int ia = tile.y + ta, ip = tile.z + tp;
     if (ia >= na || ip >= np) return;
     int id[6];
@@ -701,7 +710,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     T F[7];
     T* bp = sm + kNSlot * NCMAX + tid;      // this thread's back-projection slots
     JsWeights<T, Z> js;
-    interface_flux<T>(sm, NC, id, T(A.gamma), bp, 256, js, F);
+    interface_flux<T>(sm, NC, id, T(A.gamma), bp, kSweepNT, js, F);
 
     // rotate back and store at the lower face of cell ia
     int i, j, k;
@@ -728,7 +737,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
 // table; each tile carries its shape, read by one body with the shape as a
 // block-uniform runtime value, so patches of uneven sizes share one launch.
 template <class T, int AXIS, bool Z>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
+__global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
     constexpr int NCMAX = max_nc(AXIS);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -757,7 +766,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
 // One tile per block, default shape, Jiang-Shu weights: the launch for tile
 // tables that use shape 0 throughout (a single grid, or patches tuned to it).
 template <class T, int AXIS>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel_fixed(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel_fixed(const SweepArgs<T> A) {
     constexpr int NC0 = nc_of(shape_ta(AXIS, 0));
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -769,7 +778,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel_fixed(c
 
 template <class T, int AXIS>
 constexpr size_t smem_bytes_fixed() {
-    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNBack * 256);
+    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNBack * kSweepNT);
 }
 
 template <class T, int AXIS>
@@ -780,7 +789,7 @@ constexpr size_t smem_bytes() {
 
 template <class T, int AXIS>
 constexpr size_t smem_bytes_persistent() {
-    return sizeof(T) * (kNSlot * max_nc(AXIS) + kNBack * 256);
+    return sizeof(T) * (kNSlot * max_nc(AXIS) + kNBack * kSweepNT);
 }
 
 }  // namespace
@@ -797,11 +806,14 @@ template <class T>
 int sweep_blocks_per_sm(int axis) {
     int nb = 0;
     if (axis == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 0, false>, 256, smem_bytes_persistent<T, 0>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 0, false>, kSweepNT,
+                                                      smem_bytes_persistent<T, 0>());
     else if (axis == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 1, false>, 256, smem_bytes_persistent<T, 1>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 1, false>, kSweepNT,
+                                                      smem_bytes_persistent<T, 1>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 2, false>, 256, smem_bytes_persistent<T, 2>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, 2, false>, kSweepNT,
+                                                      smem_bytes_persistent<T, 2>());
     return nb > 0 ? nb : 1;
 }
 
@@ -846,9 +858,9 @@ template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (a.uniform_shape0 && !a.zweights) {
-        if (axis == 0) sweep_kernel_fixed<T, 0><<<ntiles, 256, smem_bytes_fixed<T, 0>(), s>>>(a);
-        else if (axis == 1) sweep_kernel_fixed<T, 1><<<ntiles, 256, smem_bytes_fixed<T, 1>(), s>>>(a);
-        else sweep_kernel_fixed<T, 2><<<ntiles, 256, smem_bytes_fixed<T, 2>(), s>>>(a);
+        if (axis == 0) sweep_kernel_fixed<T, 0><<<ntiles, kSweepNT, smem_bytes_fixed<T, 0>(), s>>>(a);
+        else if (axis == 1) sweep_kernel_fixed<T, 1><<<ntiles, kSweepNT, smem_bytes_fixed<T, 1>(), s>>>(a);
+        else sweep_kernel_fixed<T, 2><<<ntiles, kSweepNT, smem_bytes_fixed<T, 2>(), s>>>(a);
         return cudaGetLastError();
     }
     const int grid = PersistGrid<T>::g[axis] > 0 ? PersistGrid<T>::g[axis] : 152;
@@ -858,14 +870,14 @@ cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream
         if (e != cudaSuccess) return e;
     }
     if (a.zweights) {
-        if (axis == 0) sweep_kernel<T, 0, true><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
-        else if (axis == 1) sweep_kernel<T, 1, true><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
-        else sweep_kernel<T, 2, true><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
+        if (axis == 0) sweep_kernel<T, 0, true><<<nb, kSweepNT, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
+        else if (axis == 1) sweep_kernel<T, 1, true><<<nb, kSweepNT, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
+        else sweep_kernel<T, 2, true><<<nb, kSweepNT, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
         return cudaGetLastError();
     }
-    if (axis == 0) sweep_kernel<T, 0, false><<<nb, 256, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
-    else if (axis == 1) sweep_kernel<T, 1, false><<<nb, 256, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
-    else sweep_kernel<T, 2, false><<<nb, 256, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
+    if (axis == 0) sweep_kernel<T, 0, false><<<nb, kSweepNT, smem_bytes_persistent<T, 0>(), s>>>(a, ntiles);
+    else if (axis == 1) sweep_kernel<T, 1, false><<<nb, kSweepNT, smem_bytes_persistent<T, 1>(), s>>>(a, ntiles);
+    else sweep_kernel<T, 2, false><<<nb, kSweepNT, smem_bytes_persistent<T, 2>(), s>>>(a, ntiles);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@ namespace wb {
 
 void sweep_shape(int axis, int s, int* ta, int* tp) {
     *ta = shape_ta(axis, s);
-    *tp = 256 / *ta;
+    *tp = kSweepNT / *ta;
 }
 
 template cudaError_t prepare_sweep_kernels<double>();
