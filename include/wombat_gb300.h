@@ -146,6 +146,13 @@ int wb_cfl_dt(wb_grid *g, double cfl, double *dt_out);
  * Also reports a non-finite state seen by an earlier asynchronous step. */
 int wb_conserved_totals(wb_grid *g, double out[8]);
 
+/* Face divergence of the magnetic field, the invariant of the constrained
+ * transport (Sec. 2.1): out[0] = max over cells of |(bx(i+1)-bx(i))/dx +
+ * (by(j+1)-by(j))/dy + (bz(k+1)-bz(k))/dz| (neighbouring faces across patch
+ * links or periodic wrap), out[1] = max |b| over the faces, both in FP64.
+ * Synchronises.  Errors: WB_EINVAL (null argument), WB_ECUDA. */
+int wb_div_b(wb_grid *g, double out[2]);
+
 /* Copy the state to host arrays of the wb_init_grid layout (FP64).
  * Either pointer may be NULL to skip it.  Synchronises. */
 int wb_get_state(wb_grid *g, double *U_out, double *b_out);

@@ -734,6 +734,26 @@ int wb_cfl_dt(wb_grid* g, double cfl, double* dt_out) {
     return WB_OK;
 }
 
+int wb_div_b(wb_grid* g, double out[2]) {
+    g_err.clear();
+    if (!g || !out) return fail(WB_EINVAL, "null argument");
+    WB_CK(cudaSetDevice(g->device));
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(g->d_partial + kPartials * 8);
+    if (g->precision == WB_FP64)
+        WB_CK(wb::launch_divb<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches,
+                                      g->d_links, g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy,
+                                      1.0 / g->dz, bits, g->d_flag, g->stream));
+    else
+        WB_CK(wb::launch_divb<float>(static_cast<const float*>(g->un), g->d_blocks, g->d_patches,
+                                     g->d_links, g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy,
+                                     1.0 / g->dz, bits, g->d_flag, g->stream));
+    WB_CK(cudaMemcpyAsync(g->h_small + 2, bits, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->stream));
+    const int rc = check_flag(g);
+    if (rc != WB_OK) return rc;
+    std::memcpy(out, g->h_small + 2, sizeof(double) * 2);
+    return WB_OK;
+}
+
 int wb_conserved_totals(wb_grid* g, double out[8]) {
     g_err.clear();
     if (!g || !out) return fail(WB_EINVAL, "null argument");

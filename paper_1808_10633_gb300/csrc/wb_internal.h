@@ -162,6 +162,10 @@ cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* 
                        const int* links, long long ncells, int nblocks, double idx, double idy, double idz,
                        double gamma, unsigned long long* smax_bits, unsigned int* flag,
                        cudaStream_t s);
+template <class T>
+cudaError_t launch_divb(const T* state, const CellBlock* blocks, const PatchDev* patches,
+                        const int* links, long long ncells, int nblocks, double idx, double idy,
+                        double idz, unsigned long long* out_bits, unsigned int* flag, cudaStream_t s);
 cudaError_t launch_set_dt(const unsigned long long* smax_bits, double cfl, double fixed_dt,
                           double* dt, double* time, cudaStream_t s);
 

@@ -97,6 +97,49 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
     }
 }
 
+// Face divergence of b per cell (the quantity constrained transport keeps at
+// round-off, Sec. 2.1): (bx(i+1) - bx(i))/dx + (by(j+1) - by(j))/dy +
+// (bz(k+1) - bz(k))/dz, in FP64; out_bits[0] = max |div b|, out_bits[1] =
+// max |b| over the faces, both as FP64 bit patterns (non-negative values, so
+// an integer maximum orders them).
+template <class T, bool LINKED>
+__global__ void __launch_bounds__(kCellBlock)
+divb_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nblocks,
+            const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
+            double idx, double idy, double idz, unsigned long long* out_bits, unsigned int* flag) {
+    double dmax = 0.0, bmax = 0.0;
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const CellBlock cb = blocks[b];
+        const PatchDev P = patches[cb.x];
+        const int local = cb.y + threadIdx.x;
+        const int nxy = P.nx * P.ny;
+        if (local < nxy * P.nz) {
+            const int k = local / nxy;
+            const int rem = local - k * nxy;
+            const int j = rem / P.nx;
+            const int i = rem - j * P.nx;
+            const long long c = chk(P.off + local, N, flag);
+            const long long cx = chk(upper<LINKED>(patches, links, cb.x, P, i + 1, j, k), N, flag);
+            const long long cy = chk(upper<LINKED>(patches, links, cb.x, P, i, j + 1, k), N, flag);
+            const long long cz = chk(upper<LINKED>(patches, links, cb.x, P, i, j, k + 1), N, flag);
+            const double bx = double(q[5 * N + c]), by = double(q[6 * N + c]), bz = double(q[7 * N + c]);
+            const double d = (double(q[5 * N + cx]) - bx) * idx + (double(q[6 * N + cy]) - by) * idy
+                           + (double(q[7 * N + cz]) - bz) * idz;
+            dmax = fmax(dmax, fabs(d));
+            bmax = fmax(bmax, fmax(fabs(bx), fmax(fabs(by), fabs(bz))));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out_bits, (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(out_bits + 1, (unsigned long long)__double_as_longlong(bmax));
+    }
+}
+
 __global__ void set_dt_kernel(const unsigned long long* smax_bits, double cfl, double fixed_dt,
                               double* dt, double* time) {
     double d = fixed_dt;
@@ -282,6 +325,27 @@ cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* 
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_divb(const T* state, const CellBlock* blocks, const PatchDev* patches,
+                        const int* links, long long ncells, int nblocks, double idx, double idy,
+                        double idz, unsigned long long* out_bits, unsigned int* flag, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cap = 8 * (nsm > 0 ? nsm : 152);
+    const int grid = nblocks < cap ? nblocks : cap;
+    if (links)
+        divb_kernel<T, true><<<grid, kCellBlock, 0, s>>>(state, blocks, nblocks, patches, links, ncells,
+                                                         idx, idy, idz, out_bits, flag);
+    else
+        divb_kernel<T, false><<<grid, kCellBlock, 0, s>>>(state, blocks, nblocks, patches, links, ncells,
+                                                          idx, idy, idz, out_bits, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_dt(const unsigned long long* smax_bits, double cfl, double fixed_dt,
                           double* dt, double* time, cudaStream_t s) {
     set_dt_kernel<<<1, 1, 0, s>>>(smax_bits, cfl, fixed_dt, dt, time);
@@ -321,6 +385,9 @@ cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock*
     template cudaError_t launch_cfl<T>(const T*, const CellBlock*, const PatchDev*, const int*, \
                                        long long, int, double, double, double, double,       \
                                        unsigned long long*, unsigned int*, cudaStream_t);     \
+    template cudaError_t launch_divb<T>(const T*, const CellBlock*, const PatchDev*, const int*, \
+                                        long long, int, double, double, double,              \
+                                        unsigned long long*, unsigned int*, cudaStream_t);    \
     template cudaError_t launch_totals<T>(const T*, const PatchDev*, int, long long, double*, \
                                           int, double, double*, cudaStream_t);                \
     template cudaError_t launch_import<T>(const double*, const double*, T*, const CellBlock*, \

@@ -28,7 +28,7 @@ EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt"
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
            "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune",
-           "wb_learned_stats")
+           "wb_learned_stats", "wb_div_b")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
     L.wb_set_mlp.argtypes = [vp, vp, d, d]
     L.wb_autotune.argtypes = [vp, vp]
     L.wb_learned_stats.argtypes = [vp, vp, i]
+    L.wb_div_b.argtypes = [vp, dp]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
@@ -207,6 +208,12 @@ class Grid:
         out = (ctypes.c_double * 8)()
         _check(self._lib.wb_conserved_totals(self._h, out))
         return np.array(out[:])
+
+    def div_b(self):
+        """(max |face divergence of b|, max |b| over faces), FP64."""
+        out = (ctypes.c_double * 2)()
+        _check(self._lib.wb_div_b(self._h, out))
+        return float(out[0]), float(out[1])
 
     def get_state(self, U_out=None, b_out=None):
         """Returns (U, b) as flat float64 arrays (or fills the given buffers)."""

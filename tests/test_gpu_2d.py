@@ -121,3 +121,24 @@ def test_orszag_tang_pressure_converges_and_fp32_tracks(wb):
     l1 = np.abs(pressure(U32, st.gamma)[0] - p[128]).mean() / np.abs(p[128]).mean()
     print("Orszag-Tang 128^2 t=0.5 FP32 vs FP64 pressure L1: %.2e" % l1)
     assert l1 <= 1e-3
+
+
+def test_monitor_log_lines(wb):
+    """The run monitor lands on t_end and logs conserved totals, div b and
+    throughput as JSON lines."""
+    import json
+
+    from paper_1808_10633_gb300 import monitor
+
+    st = I.orszag_tang(64)
+    g = wb.Grid.from_state(st, precision="fp32")
+    lines = []
+    last = monitor.run(g, t_end=0.1, every=10, emit=lines.append, hmin=st.dx)
+    g.close()
+    recs = [json.loads(x) for x in lines]
+    assert recs[-1] == last and abs(last["t"] - 0.1) < 1e-12
+    assert all(r["div_b_rel"] < 1e-5 for r in recs)
+    t0 = np.array(recs[0]["totals"])
+    for r in recs[1:]:
+        assert np.allclose(r["totals"], t0, rtol=1e-6, atol=1e-9)
+        assert r["zone_updates_per_s"] > 0

@@ -275,3 +275,31 @@ def test_fp64_weno_z_weights_match_oracle(orc, wb):
     # and they differ from the Jiang-Shu result
     Uj = orc.step(ogrid(orc, st), st.U, st.bx, st.by, st.bz, 2e-3, nsteps=2)[0]
     assert rel_err(Uj, Uo).max() > 1e3 * TOL64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_div_b_diagnostic_matches_oracle(orc, wb, precision):
+    """wb_div_b against the oracle's face divergence: a field that is not
+    solenoidal gives the same maximum; the CT keeps a solenoidal one at
+    round-off through steps (also on linked bricks)."""
+    from paper_1808_10633_gb300 import bricks
+
+    rng = np.random.default_rng(8)
+    st = I.perturbed(20, 16, 12, seed=5)
+    og = ogrid(orc, st)
+    bad = st.copy()
+    bad.bx = bad.bx + 0.01 * rng.standard_normal(bad.bx.shape)
+    g = wb.Grid.from_state(bad, precision=precision)
+    dmax, bmax = g.div_b()
+    g.close()
+    ref = np.abs(orc.div_b(og, bad.bx, bad.by, bad.bz)).max()
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert dmax == pytest.approx(ref, rel=tol)
+    assert bmax == pytest.approx(max(np.abs(bad.bx).max(), np.abs(bad.by).max(), np.abs(bad.bz).max()), rel=1e-7)
+    scale = bmax / min(st.dx, st.dy, st.dz)
+    for g in (wb.Grid.from_state(st, precision=precision),
+              wb.Grid.from_bricks(st, ([0, 9, 20], [0, 7, 16], [0, 12]), precision=precision)):
+        g.step_cfl(0.4, 5)
+        d, _ = g.div_b()
+        assert d <= (1e-13 if precision == "fp64" else 1e-5) * scale, d / scale
+        g.close()
