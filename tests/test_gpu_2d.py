@@ -140,5 +140,5 @@ def test_monitor_log_lines(wb):
     assert all(r["div_b_rel"] < 1e-5 for r in recs)
     t0 = np.array(recs[0]["totals"])
     for r in recs[1:]:
-        assert np.allclose(r["totals"], t0, rtol=1e-6, atol=1e-9)
+        assert np.allclose(r["totals"], t0, rtol=1e-6, atol=1e-7)
         assert r["zone_updates_per_s"] > 0
