@@ -335,7 +335,12 @@ std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
             }
         }
         int ta, tp;
-        wb::sweep_shape(axis, best, &ta, &tp);
+        if (g->precision == WB_FP32_LEARNED) {
+            wb::learned_shape(axis, &ta, &tp);     // the learned sweep's own tile
+            best = 0;
+        } else {
+            wb::sweep_shape(axis, best, &ta, &tp);
+        }
         const int px = p | (best << 24);
         if (axis == 0) {
             for (int z = 0; z < P.nz; z++)

@@ -138,6 +138,8 @@ cudaError_t prepare_sweep_kernels();
 // `axis`: ta interfaces along the axis times tp pencils (ta * tp = 256).
 constexpr int kNTileShape = 3;
 void sweep_shape(int axis, int s, int* ta, int* tp);
+// Tile of the learned-weight sweep along `axis` (one shape, 256 threads).
+void learned_shape(int axis, int* ta, int* tp);
 
 template <class T>
 cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s);

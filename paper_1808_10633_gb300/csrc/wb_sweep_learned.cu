@@ -312,6 +312,11 @@ constexpr size_t learned_smem_bytes() {
 
 }  // namespace
 
+void learned_shape(int axis, int* ta, int* tp) {
+    *ta = axis == 0 ? Shape<0>::TA : Shape<1>::TA;
+    *tp = axis == 0 ? Shape<0>::TP : Shape<1>::TP;
+}
+
 cudaError_t prepare_sweep_learned() {
     cudaError_t e;
     e = cudaFuncSetAttribute(sweep_learned_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
