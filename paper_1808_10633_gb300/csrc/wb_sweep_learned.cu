@@ -173,10 +173,12 @@ struct LearnedWeights {
             for (int k = 0; k < 6; k++) mx = fmaxf(mx, fabsf(v[k] - mean));
             const float inv = __fdividef(1.0f, mx + 1e-12f);
             const int r = 2 * lane + side;
-            in[r * 4 + 0] = pack_bf16((v[0] - mean) * inv, (v[1] - mean) * inv);
-            in[r * 4 + 1] = pack_bf16((v[2] - mean) * inv, (v[3] - mean) * inv);
-            in[r * 4 + 2] = pack_bf16((v[4] - mean) * inv, (v[5] - mean) * inv);
-            in[r * 4 + 3] = pack_bf16(1.0f, 0.0f);
+            // one 16-byte store per row (four 4-byte stores at an 8-word lane
+            // stride would meet in 4 banks)
+            *reinterpret_cast<uint4*>(in + r * 4) =
+                make_uint4(pack_bf16((v[0] - mean) * inv, (v[1] - mean) * inv),
+                           pack_bf16((v[2] - mean) * inv, (v[3] - mean) * inv),
+                           pack_bf16((v[4] - mean) * inv, (v[5] - mean) * inv), pack_bf16(1.0f, 0.0f));
             const float* D = side == 0 ? Dp : Dm;
             float a[4], dmax = 0.f, dsum = 0.f;
 #pragma unroll
@@ -187,8 +189,8 @@ struct LearnedWeights {
         __syncwarp();
         mlp_warp(W + s * kMlpWords * 32, in, om, lane);
         __syncwarp();
-        const float w0p = om[4 * lane], w2p = om[4 * lane + 1];
-        const float w0m = om[4 * lane + 2], w2m = om[4 * lane + 3];
+        const float4 wl = *reinterpret_cast<const float4*>(om + 4 * lane);
+        const float w0p = wl.x, w2p = wl.y, w0m = wl.z, w2m = wl.w;
         __syncwarp();
         const float php = fire[0] ? phi_n(Dp[0], Dp[1], Dp[2], Dp[3])
                                   : w0p * (Dp[0] - 2.f * Dp[1] + Dp[2]) * (1.f / 3.f)
