@@ -15,9 +15,10 @@
 // fragments are re-packed in registers as the next layer's A fragments; the
 // weights sit in shared memory already in B-fragment order (34 words per lane
 // per field, written by wb_set_mlp on the host side).  GELU uses the
-// hardware tanh approximation on BF16 pairs.  Batch rows are independent, so a lane whose
-// interface lies outside the patch still joins the warp-wide products (with
-// a valid stencil) and only skips its store.
+// hardware tanh approximation on BF16 pairs and returns twice its value;
+// the hidden and output weights are stored halved to match.  Batch rows are
+// independent, so a lane whose interface lies outside the patch still joins
+// the warp-wide products (with a valid stencil) and only skips its store.
 #include "wb_sweep.cuh"
 
 #include <cuda_bf16.h>
@@ -53,22 +54,21 @@ __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], u
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// GELU of two FP32 accumulators, returned as the next layer's BF16 operand
-// pair.  The whole formula runs on the packed pair in BF16 (its result is
-// rounded to BF16 anyway): u = c x (1 + 0.044715 x^2), t = tanh(u),
-// gelu = 0.5 x (1 + t).
-__device__ __forceinline__ uint32_t gelu2(float a, float b) {
+// Twice the GELU of two FP32 accumulators, returned as the next layer's BF16
+// operand pair: with u = c x (1 + 0.044715 x^2), t = tanh(u), the pair
+// x + x t = 2 gelu(x), on the packed pair in BF16 (its result is rounded to
+// BF16 anyway).  The factor 2 is taken out of the next layer's weights, which
+// the host stores halved (exact in BF16), so the layer sees W gelu(x).
+__device__ __forceinline__ uint32_t gelu2x(float a, float b) {
     const uint32_t x = pack_bf16(a, b);
-    const uint32_t c1 = pack_bf16(0.044715f, 0.044715f), one = pack_bf16(1.0f, 1.0f);
-    const uint32_t cg = pack_bf16(0.7978845608f, 0.7978845608f), half = pack_bf16(0.5f, 0.5f);
-    uint32_t x2, p, u, t, h, r;
+    const uint32_t k0 = pack_bf16(0.7978845608f, 0.7978845608f);                 // sqrt(2/pi)
+    const uint32_t k1 = pack_bf16(0.7978845608f * 0.044715f, 0.7978845608f * 0.044715f);
+    uint32_t x2, p, u, t, r;
     asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(x2) : "r"(x));
-    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(x2), "r"(c1), "r"(one));   // 1 + c1 x^2
-    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(x), "r"(cg));
-    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(u), "r"(p));                     // c x (1 + c1 x^2)
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(x2), "r"(k1), "r"(k0));    // c (1 + 0.044715 x^2)
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(x), "r"(p));
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(u));
-    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(x), "r"(half));
-    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));                // h + h t
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(x), "r"(t));                // x + x t
     return r;
 }
 
@@ -91,10 +91,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
         uint32_t A2[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A2[kt][0] = gelu2(c1[2 * kt][0], c1[2 * kt][1]);
-            A2[kt][1] = gelu2(c1[2 * kt][2], c1[2 * kt][3]);
-            A2[kt][2] = gelu2(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
-            A2[kt][3] = gelu2(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
+            A2[kt][0] = gelu2x(c1[2 * kt][0], c1[2 * kt][1]);
+            A2[kt][1] = gelu2x(c1[2 * kt][2], c1[2 * kt][3]);
+            A2[kt][2] = gelu2x(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
+            A2[kt][3] = gelu2x(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
         }
         float c2[4][4];
 #pragma unroll
@@ -109,10 +109,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
         uint32_t A3[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A3[kt][0] = gelu2(c2[2 * kt][0], c2[2 * kt][1]);
-            A3[kt][1] = gelu2(c2[2 * kt][2], c2[2 * kt][3]);
-            A3[kt][2] = gelu2(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
-            A3[kt][3] = gelu2(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
+            A3[kt][0] = gelu2x(c2[2 * kt][0], c2[2 * kt][1]);
+            A3[kt][1] = gelu2x(c2[2 * kt][2], c2[2 * kt][3]);
+            A3[kt][2] = gelu2x(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
+            A3[kt][3] = gelu2x(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
         }
         const float b3lo = Wf[32 * 32 + lane], b3hi = Wf[33 * 32 + lane];
         float c3[4] = {b3lo, b3hi, b3lo, b3hi};
@@ -370,7 +370,7 @@ void mlp_fragments(const float* params, uint32_t* out) {
         const float* b3 = W3 + 3 * NH;
         // first layer as 32 x 8: six weights, the bias, a zero
         auto w1 = [&](int n, int k) { return k < NIN ? W1[n * NIN + k] : (k == NIN ? b1[n] : 0.f); };
-        auto w3 = [&](int n, int k) { return n < 3 ? W3[n * NH + k] : 0.f; };
+        auto w3 = [&](int n, int k) { return n < 3 ? 0.5f * W3[n * NH + k] : 0.f; };
         for (int lane = 0; lane < 32; lane++) {
             const int g = lane >> 2, t = lane & 3;
             uint32_t* o = out + (size_t)f * kMlpWords * 32 + lane;
@@ -378,8 +378,9 @@ void mlp_fragments(const float* params, uint32_t* out) {
             for (int nt = 0; nt < 4; nt++)
                 for (int kt = 0; kt < 2; kt++) {
                     const int n = 8 * nt + g, k0 = 16 * kt + 2 * t;
-                    o[(4 + nt * 4 + kt * 2) * 32] = pk(W2[n * NH + k0], W2[n * NH + k0 + 1]);
-                    o[(5 + nt * 4 + kt * 2) * 32] = pk(W2[n * NH + k0 + 8], W2[n * NH + k0 + 9]);
+                    // hidden and output weights halved: the kernel's GELU returns 2 gelu
+                    o[(4 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0], 0.5f * W2[n * NH + k0 + 1]);
+                    o[(5 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0 + 8], 0.5f * W2[n * NH + k0 + 9]);
                 }
             for (int kt = 0; kt < 2; kt++) {
                 const int k0 = 16 * kt + 2 * t;
