@@ -142,6 +142,30 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def cur_stream():
+    import torch
+
+    return torch.cuda.current_stream()
+
+
+def graph_steps_ms(g, k, cfl, world):
+    """k steps of grid g (created on torch's current stream) replayed from
+    its step graph, timed with CUDA events on that stream between barriers."""
+    import torch
+
+    stream = cur_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step_cfl(cfl, k)
+    e1.record(stream)
+    e1.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1)
+
+
 def sweep_units(n):
     """(interfaces, staged cells) per launch of each sweep kernel at n^3."""
     from paper_1808_10633_gb300 import wombat  # noqa: F401  (library must load)
@@ -167,38 +191,53 @@ def run_native(args, rank, world, local):
     peak64 = wombat.alu_peak_tflops("fp64") if not args.fp32_only else None
 
     # ---- FP32 bulk (headline) -------------------------------------------
-    g32 = wombat.Grid.from_state(st, precision="fp32")
-    for _ in range(args.warmup):
-        g32.step_cfl(args.cfl, 1)
-        g32.totals()
-    g32.sync()
+    # The grid runs on torch's current stream, so torch's CUDA events on that
+    # stream bracket the step graphs.  A step = CFL dt, three SSP-RK3 stages
+    # (sweeps, EMFs, updates) and the FP64 conserved totals of its start
+    # state (on a second stream inside the step graph).
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_steps(g, k):
+        g.sync()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.step_cfl(args.cfl, k)
+        ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        return ev0.elapsed_time(ev1)
+
+    g32 = wombat.Grid.from_state(st, precision="fp32", stream=stream.cuda_stream)
+    g32.set_step_totals(True)
+    g32.step_cfl(args.cfl, args.warmup)
     with clocks:
-        barrier(world)
-        torch.cuda.synchronize()
-        tot_ms, kms, kcnt = g32.step_profiled(args.cfl, args.steps, with_totals=True)
-        torch.cuda.synchronize()
-        barrier(world)
+        tot_ms = timed_steps(g32, args.steps)
         # FP64 path inside the same clock window
         g64 = None
         if not args.fp32_only:
-            g64 = wombat.Grid.from_state(st, precision="fp64")
+            g64 = wombat.Grid.from_state(st, precision="fp64", stream=stream.cuda_stream)
+            g64.set_step_totals(True)
             g64.step_cfl(args.cfl, 1)
-            g64.sync()
             k64 = max(2, args.steps // 4)
-            tot64, kms64, kcnt64 = g64.step_profiled(args.cfl, k64, with_totals=True)
+            tot64 = timed_steps(g64, k64)
     secs = max_over_ranks(tot_ms / 1e3, world)
     value = world * zones * args.steps / secs
     if g64 is not None:
         secs64 = max_over_ranks(tot64 / 1e3, world)
         value64 = world * zones * k64 / secs64
     clk = clocks.summary()
+    step_totals = g32.step_totals()
 
-    # graph-replay timing of the same step (no per-kernel events)
+    # per-kernel split of the same step (CUDA events around every launch,
+    # kernels serialised, totals on the same stream)
     g32.sync()
-    t0 = time.perf_counter()
-    g32.step_cfl(args.cfl, args.steps)
-    g32.sync()
-    graph_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    prof_ms, kms, kcnt = g32.step_profiled(args.cfl, args.steps, with_totals=True)
+    if g64 is not None:
+        g64.sync()
+        _, kms64, kcnt64 = g64.step_profiled(args.cfl, k64, with_totals=True)
 
     def roofline(kms_, kcnt_, peak_tflops, label):
         cls = max((k for k in ("sweep_x", "sweep_y", "sweep_z")), key=lambda k: kms_[k])
@@ -300,10 +339,13 @@ def run_native(args, rank, world, local):
                    "grid": [n, n, n], "precision": "fp32-bulk (fp64 islands)",
                    "l2": "inputs larger than L2 (state 8 x 64 MiB fp32 + fluxes)",
                    "parallelism": f"replicas x{world}"},
-        "gpu_launches": int(sum(kcnt.values())),
+        # kernels in the timed region: per step the profiled classes, with the
+        # totals class counting its two kernels
+        "gpu_launches": int(sum(kcnt.values()) + kcnt.get("totals", 0)),
         "launches_per_step": launches_per_step,
-        "graph_replay_ms_per_step": graph_ms,
+        "profiled_ms_per_step": prof_ms / args.steps,
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "step_totals_last": step_totals.tolist(),
         "roofline": rf32,
         "fp64": None if g64 is None else
                 {"value": value64, "unit": UNIT, "ms_per_step": secs64 * 1e3 / k64, "steps": k64,
@@ -333,30 +375,21 @@ def run_patches(args, world):
     sts = inputs.patch_batch(args.patches, seed=1808)
     t_gen = time.perf_counter() - t0
     cells = sum(s.U[0].size for s in sts)
-    g = wombat.Grid.from_patches(sts, precision="fp32")
-    for _ in range(args.warmup):
-        g.step_cfl(args.cfl, 1)
-    g.sync()
-    tot0, kms0, _ = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    g = wombat.Grid.from_patches(sts, precision="fp32", stream=cur_stream().cuda_stream)
+    g.set_step_totals(True)
+    g.step_cfl(args.cfl, args.warmup)
+    tot0 = graph_steps_ms(g, args.steps, args.cfl, world)      # cost-model tiles
     tune = g.autotune()
-    for _ in range(2):
-        g.step_cfl(args.cfl, 1)
-    g.sync()
-    barrier(world)
-    torch.cuda.synchronize()
-    tot, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
-    barrier(world)
+    g.step_cfl(args.cfl, 2)
+    tot = graph_steps_ms(g, args.steps, args.cfl, world)
     secs = max_over_ranks(tot / 1e3, world)
     g.sync()
-    t1 = time.perf_counter()
-    g.step_cfl(args.cfl, args.steps)       # CUDA-graph replay
-    g.sync()
-    graph_ms = (time.perf_counter() - t1) * 1e3 / args.steps
+    _, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
     g.close()
     return {"workload": f"{args.patches} periodic patches, edges log-uniform in [16,64], "
                         "Brio-Wu or turbulence, FP32", "cells": int(cells),
             "value": world * cells * args.steps / secs, "unit": UNIT,
-            "ms_per_step": secs * 1e3 / args.steps, "graph_replay_ms_per_step": graph_ms,
+            "ms_per_step": secs * 1e3 / args.steps,
             "ms_per_step_cost_model_tiles": tot0 / args.steps,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
@@ -374,20 +407,16 @@ def run_linked(args, st, world):
     n = args.size
     cut = lambda f: [0] + [int(round(n * x)) for x in f] + [n]
     cuts = (cut([0.22, 0.47, 0.74]), cut([0.27, 0.5, 0.77]), cut([0.24, 0.53, 0.76]))
-    g = wombat.Grid.from_bricks(st, cuts, precision="fp32")
-    for _ in range(args.warmup):
-        g.step_cfl(args.cfl, 1)
-    g.sync()
-    tot0, _, _ = g.step_profiled(args.cfl, args.steps, with_totals=True)
+    g = wombat.Grid.from_bricks(st, cuts, precision="fp32", stream=cur_stream().cuda_stream)
+    g.set_step_totals(True)
+    g.step_cfl(args.cfl, args.warmup)
+    tot0 = graph_steps_ms(g, args.steps, args.cfl, world)      # cost-model tiles
     tune = g.autotune()
-    for _ in range(2):
-        g.step_cfl(args.cfl, 1)
-    g.sync()
-    barrier(world)
-    torch.cuda.synchronize()
-    tot, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
-    barrier(world)
+    g.step_cfl(args.cfl, 2)
+    tot = graph_steps_ms(g, args.steps, args.cfl, world)
     secs = max_over_ranks(tot / 1e3, world)
+    g.sync()
+    _, kms, kcnt = g.step_profiled(args.cfl, args.steps, with_totals=True)
     g.close()
     return {"workload": f"turbulence {n}^3 as 64 linked bricks (cuts {cuts}), FP32",
             "value": world * n ** 3 * args.steps / secs, "unit": UNIT,
@@ -408,20 +437,19 @@ def run_large(args, world):
     t0 = time.perf_counter()
     st = inputs.add_blasts(inputs.turbulence(n, seed=1808), seed=1808, nblast=64)
     t_gen = time.perf_counter() - t0
-    g = wombat.Grid.from_state(st, precision="fp32")
+    g = wombat.Grid.from_state(st, precision="fp32", stream=cur_stream().cuda_stream)
+    g.set_step_totals(True)
     blast_cells = st.meta.get("blast_cells")
     del st
     steps = max(2, args.large_steps)
-    for _ in range(args.warmup):
-        g.step_cfl(args.cfl, 1)
+    g.step_cfl(args.cfl, args.warmup)
+    tot = graph_steps_ms(g, steps, args.cfl, world)
+    secs = max_over_ranks(tot / 1e3, world)
     g.sync()
-    barrier(world)
-    torch.cuda.synchronize()
-    tot, kms, kcnt = g.step_profiled(args.cfl, steps, with_totals=True)
-    barrier(world)
+    # the sweeps' own time from CUDA events around each launch
+    _, kms, kcnt = g.step_profiled(args.cfl, steps, with_totals=True)
     sweep_ms = sum(kms[k] for k in ("sweep_x", "sweep_y", "sweep_z"))
     sweep_s = max_over_ranks(sweep_ms / 1e3, world)
-    secs = max_over_ranks(tot / 1e3, world)
     try:
         finite = bool(np.isfinite(g.totals()).all())
     except wombat.WombatError:
@@ -462,19 +490,17 @@ def run_learned(args, st, world, peak32):
     st5 = inputs.add_blasts(st, seed=1808, nblast=64)
     n = args.size
     zones = n ** 3
-    gl = wombat.Grid.from_state(st5, precision="learned")
+    gl = wombat.Grid.from_state(st5, precision="learned", stream=cur_stream().cuda_stream)
     gl.set_mlp(params, 4.0, 0.5)
-    for _ in range(args.warmup):
-        gl.step_cfl(args.cfl, 1)
-    gl.sync()
-    barrier(world)
-    torch.cuda.synchronize()
+    gl.set_step_totals(True)
+    gl.step_cfl(args.cfl, args.warmup)
     gl.learned_stats(reset=True)
-    tot, kms, kcnt = gl.step_profiled(args.cfl, args.steps, with_totals=True)
-    barrier(world)
+    tot = graph_steps_ms(gl, args.steps, args.cfl, world)
     secs = max_over_ranks(tot / 1e3, world)
     value = world * zones * args.steps / secs
     fired, decisions = gl.learned_stats(reset=True)
+    gl.sync()
+    _, kms, kcnt = gl.step_profiled(args.cfl, args.steps, with_totals=True)
     # MLP work: 14 evaluations (7 fields x 2 sides) of 2*(6*32+32*32+32*3) flops per interface
     mlp_flops = 14 * 2 * (6 * 32 + 32 * 32 + 32 * 3) * zones
     cls = max(("sweep_x", "sweep_y", "sweep_z"), key=lambda k: kms[k])

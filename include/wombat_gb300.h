@@ -146,6 +146,18 @@ int wb_cfl_dt(wb_grid *g, double cfl, double *dt_out);
  * Also reports a non-finite state seen by an earlier asynchronous step. */
 int wb_conserved_totals(wb_grid *g, double out[8]);
 
+/* Per-step totals: with on != 0 every step (wb_step, wb_step_cfl) also
+ * takes the conserved totals of its start state, on a second stream beside
+ * the CFL kernel and the first Runge-Kutta stages (joined before the last
+ * stage overwrites the state), so they cost little step time.  Synchronises
+ * when the setting changes.  Errors: WB_EINVAL, WB_ECUDA. */
+int wb_set_step_totals(wb_grid *g, int on);
+
+/* The per-step totals of the last step taken (the state at that step's
+ * start; layout as wb_conserved_totals).  Synchronises.  Errors: WB_EINVAL
+ * (null argument, per-step totals off), WB_ENONFINITE as wb_cfl_dt. */
+int wb_step_totals(wb_grid *g, double out[8]);
+
 /* Face divergence of the magnetic field, the invariant of the constrained
  * transport (Sec. 2.1): out[0] = max over cells of |(bx(i+1)-bx(i))/dx +
  * (by(j+1)-by(j))/dy + (bz(k+1)-bz(k))/dz| (neighbouring faces across patch

@@ -88,6 +88,9 @@ struct wb_grid {
     uint32_t* d_mlp = nullptr;            // learned weights, fragment order
     unsigned long long* d_lstats = nullptr;   // detector firings, decisions (learned grids)
     int* d_queue = nullptr;               // per-axis tile counters of the persistent sweeps
+    int step_totals = 0;                  // 1: every step also takes the totals of its start state
+    cudaStream_t side = nullptr;          // stream the per-step totals run on
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double kappa = 4.0, pjump = 0.5;
     int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
     int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
@@ -103,7 +106,7 @@ struct wb_grid {
     double* d_scalars = nullptr;          // dt, time
     unsigned long long* d_smax = nullptr;
     unsigned int* d_flag = nullptr;
-    double* d_partial = nullptr;          // kPartials*8 + 8 (totals)
+    double* d_partial = nullptr;          // totals partials and result slots (kTotalsSlot ...)
     double* d_io = nullptr;               // FP64 staging, 11 N
     double* h_small = nullptr;            // pinned scratch for scalars
     cudaGraphExec_t graph = nullptr;
@@ -125,6 +128,8 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
     T* er = static_cast<T*>(g->er);
     const int nstage = g->integrator == WB_RK4 ? 4 : 3;
     for (int st = 0; st < nstage; st++) {
+        // per-step totals read un on the side stream; the last stage writes un
+        if (st == nstage - 1 && g->step_totals && !pf) WB_CK(cudaStreamWaitEvent(g->stream, g->ev_join, 0));
         const T* src = st == 0 ? un : uk;
         for (int axis = 0; axis < 3; axis++) {
             wb::SweepArgs<T> a;
@@ -202,23 +207,36 @@ int enqueue_cfl(wb_grid* g, Prof* pf = nullptr) {
     return prof_end(pf, g->stream, WB_K_CFL);
 }
 
-int enqueue_totals(wb_grid* g, Prof* pf = nullptr) {
-    double* res = g->d_partial + kPartials * 8;
+// d_partial: kPartials*8 pass-1 partials, then 8 totals (wb_conserved_totals),
+// 8 per-step totals, 2 words of the div b maxima.
+constexpr int kTotalsSlot = kPartials * 8, kStepTotalsSlot = kPartials * 8 + 8, kDivbSlot = kPartials * 8 + 16;
+
+int enqueue_totals(wb_grid* g, Prof* pf = nullptr, cudaStream_t st = nullptr, int slot = kTotalsSlot) {
+    if (!st) st = g->stream;
+    double* res = g->d_partial + slot;
     const double dV = g->dx * g->dy * g->dz;
-    int rc = prof_begin(pf, g->stream);
+    int rc = prof_begin(pf, st);
     if (rc != WB_OK) return rc;
     if (g->precision == WB_FP64)
         WB_CK(wb::launch_totals<double>(static_cast<const double*>(g->un), g->d_patches, g->npatch,
-                                        g->N, g->d_partial, kPartials, dV, res, g->stream));
+                                        g->N, g->d_partial, kPartials, dV, res, st));
     else
         WB_CK(wb::launch_totals<float>(static_cast<const float*>(g->un), g->d_patches, g->npatch,
-                                       g->N, g->d_partial, kPartials, dV, res, g->stream));
-    return prof_end(pf, g->stream, WB_K_TOTALS);
+                                       g->N, g->d_partial, kPartials, dV, res, st));
+    return prof_end(pf, st, WB_K_TOTALS);
 }
 
 // One step: mode 0 fixed dt = value, mode 1 dt = value / smax.
 int enqueue_step(wb_grid* g, int mode, double value, Prof* pf = nullptr) {
     int rc;
+    if (g->step_totals && !pf) {
+        // totals of the step's start state, beside the CFL kernel and the
+        // first stages (joined before the last stage overwrites the state)
+        WB_CK(cudaEventRecord(g->ev_fork, g->stream));
+        WB_CK(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        if ((rc = enqueue_totals(g, nullptr, g->side, kStepTotalsSlot)) != WB_OK) return rc;
+        WB_CK(cudaEventRecord(g->ev_join, g->side));
+    }
     if (mode == 1) {
         if ((rc = enqueue_cfl(g, pf)) != WB_OK) return rc;
         if ((rc = prof_begin(pf, g->stream)) != WB_OK) return rc;
@@ -300,15 +318,16 @@ void release(wb_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->side) cudaStreamSynchronize(g->side);
     void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_lstats, g->d_queue,
-                    g->d_patches,
-                    g->d_links,
-                    g->d_tiles[0],
-                    g->d_tiles[1], g->d_tiles[2], g->d_blocks, g->d_vblocks, g->d_scalars, g->d_smax,
-                    g->d_flag, g->d_partial, g->d_io};
+                    g->d_patches, g->d_links, g->d_tiles[0], g->d_tiles[1], g->d_tiles[2], g->d_blocks,
+                    g->d_vblocks, g->d_scalars, g->d_smax, g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_small) cudaFreeHost(g->h_small);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->side) cudaStreamDestroy(g->side);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -622,7 +641,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if ((rc = dmalloc(g, &g->d_scalars, sizeof(double) * 2))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_smax, sizeof(unsigned long long)))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_flag, sizeof(unsigned int)))) return bail(rc);
-    if ((rc = dmalloc(g, &g->d_partial, sizeof(double) * (kPartials * 8 + 8)))) return bail(rc);
+    if ((rc = dmalloc(g, &g->d_partial, sizeof(double) * (kPartials * 8 + 18)))) return bail(rc);
     if ((rc = dmalloc(g, &g->d_io, sizeof(double) * 11 * N))) return bail(rc);
     if (g->precision == WB_FP32_LEARNED &&
         (rc = dmalloc(g, &g->d_lstats, sizeof(unsigned long long) * 2))) return bail(rc);
@@ -739,11 +758,45 @@ int wb_cfl_dt(wb_grid* g, double cfl, double* dt_out) {
     return WB_OK;
 }
 
+int wb_set_step_totals(wb_grid* g, int on) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    WB_CK(cudaSetDevice(g->device));
+    on = on ? 1 : 0;
+    if (on && !g->side) {
+        WB_CK(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+        WB_CK(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+        WB_CK(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    }
+    if (on != g->step_totals) {
+        WB_CK(cudaStreamSynchronize(g->stream));
+        g->step_totals = on;
+        if (g->graph) {             // the step changed: capture again
+            cudaGraphExecDestroy(g->graph);
+            g->graph = nullptr;
+        }
+    }
+    return WB_OK;
+}
+
+int wb_step_totals(wb_grid* g, double out[8]) {
+    g_err.clear();
+    if (!g || !out) return fail(WB_EINVAL, "null argument");
+    if (!g->step_totals) return fail(WB_EINVAL, "step totals are off (wb_set_step_totals)");
+    WB_CK(cudaSetDevice(g->device));
+    WB_CK(cudaMemcpyAsync(g->h_small + 2, g->d_partial + kStepTotalsSlot, sizeof(double) * 8,
+                          cudaMemcpyDeviceToHost, g->stream));
+    const int rc = check_flag(g);
+    if (rc != WB_OK) return rc;
+    std::memcpy(out, g->h_small + 2, sizeof(double) * 8);
+    return WB_OK;
+}
+
 int wb_div_b(wb_grid* g, double out[2]) {
     g_err.clear();
     if (!g || !out) return fail(WB_EINVAL, "null argument");
     WB_CK(cudaSetDevice(g->device));
-    unsigned long long* bits = reinterpret_cast<unsigned long long*>(g->d_partial + kPartials * 8);
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(g->d_partial + kDivbSlot);
     if (g->precision == WB_FP64)
         WB_CK(wb::launch_divb<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches,
                                       g->d_links, g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy,

@@ -28,7 +28,7 @@ EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt"
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
            "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune",
-           "wb_learned_stats", "wb_div_b")
+           "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
     L.wb_autotune.argtypes = [vp, vp]
     L.wb_learned_stats.argtypes = [vp, vp, i]
     L.wb_div_b.argtypes = [vp, dp]
+    L.wb_set_step_totals.argtypes = [vp, i]
+    L.wb_step_totals.argtypes = [vp, dp]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
@@ -207,6 +209,17 @@ class Grid:
     def totals(self) -> np.ndarray:
         out = (ctypes.c_double * 8)()
         _check(self._lib.wb_conserved_totals(self._h, out))
+        return np.array(out[:])
+
+    def set_step_totals(self, on: bool = True):
+        """Take the conserved totals of every step's start state, overlapped
+        with the step's first stages."""
+        _check(self._lib.wb_set_step_totals(self._h, int(bool(on))))
+
+    def step_totals(self) -> np.ndarray:
+        """Totals of the start state of the last step taken."""
+        out = (ctypes.c_double * 8)()
+        _check(self._lib.wb_step_totals(self._h, out))
         return np.array(out[:])
 
     def div_b(self):

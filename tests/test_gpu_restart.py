@@ -65,3 +65,28 @@ def test_runs_are_deterministic(wb, precision):
     (U2, b2), t2, d2 = out[1]
     assert np.array_equal(U1, U2) and np.array_equal(b1, b2)
     assert np.array_equal(t1, t2) and d1 == d2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_totals_overlap(wb, precision):
+    """Per-step totals (second stream inside the step graph) equal the
+    explicit totals of the state each step starts from, and leave the
+    solution bit for bit unchanged."""
+    st = I.turbulence(32, seed=15)
+    g1 = wb.Grid.from_state(st, precision=precision)
+    g2 = wb.Grid.from_state(st, precision=precision)
+    g1.set_step_totals(True)
+    g1.step_cfl(0.4, 4)
+    g2.step_cfl(0.4, 4)
+    t4 = g1.totals()
+    g1.step_cfl(0.4, 1)
+    g2.step_cfl(0.4, 1)
+    assert np.array_equal(g1.step_totals(), t4)
+    U1, b1 = g1.get_state()
+    U2, b2 = g2.get_state()
+    assert np.array_equal(U1, U2) and np.array_equal(b1, b2)
+    g1.set_step_totals(False)
+    with pytest.raises(wb.WombatError):
+        g1.step_totals()
+    g1.close()
+    g2.close()
