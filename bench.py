@@ -142,15 +142,24 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def cur_stream():
-    import torch
+_STREAM = None
 
-    return torch.cuda.current_stream()
+
+def cur_stream():
+    """The CUDA stream the benchmark's grids run on (a torch stream of its
+    own: the legacy default stream has handle 0, which the library reads as
+    "make your own stream")."""
+    global _STREAM
+    if _STREAM is None:
+        import torch
+
+        _STREAM = torch.cuda.Stream()
+    return _STREAM
 
 
 def graph_steps_ms(g, k, cfl, world):
-    """k steps of grid g (created on torch's current stream) replayed from
-    its step graph, timed with CUDA events on that stream between barriers."""
+    """k steps of grid g (created on cur_stream()) replayed from its step
+    graph, timed with CUDA events on that stream between barriers."""
     import torch
 
     stream = cur_stream()
@@ -191,11 +200,11 @@ def run_native(args, rank, world, local):
     peak64 = wombat.alu_peak_tflops("fp64") if not args.fp32_only else None
 
     # ---- FP32 bulk (headline) -------------------------------------------
-    # The grid runs on torch's current stream, so torch's CUDA events on that
-    # stream bracket the step graphs.  A step = CFL dt, three SSP-RK3 stages
+    # The grid runs on a torch stream, so torch's CUDA events on that stream
+    # bracket the step graphs.  A step = CFL dt, three SSP-RK3 stages
     # (sweeps, EMFs, updates) and the FP64 conserved totals of its start
     # state (on a second stream inside the step graph).
-    stream = torch.cuda.current_stream()
+    stream = cur_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed_steps(g, k):
