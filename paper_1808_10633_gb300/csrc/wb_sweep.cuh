@@ -33,6 +33,9 @@
 
 // Characteristic fields are projected two groups at a time (fast+slow,
 // then Alfven+entropy) by default; 4 processes one field pair at a time.
+#ifndef WB_SWEEP_PARK
+#define WB_SWEEP_PARK 1                // 1: project each stencil vector once, park the second group
+#endif
 #ifndef WB_SWEEP_GROUPS
 #define WB_SWEEP_GROUPS 2
 #endif
@@ -156,6 +159,11 @@ struct Eig {
 // Coefficients only the back-projection needs; parked in shared memory (one
 // slot per thread) while the WENO step runs, to keep registers for it.
 enum : int { BP_ALF = 0, BP_ALS, BP_AFCF, BP_ASCS, BP_ASR, BP_SSR, BP_RA2, BP_IGM1, kNBack = 8 };
+// Per-thread slots after the back-projection ones where the Alfven/entropy
+// projections (3 fields x (w, g) x 6 cells) wait while the fast/slow group
+// is reconstructed, when each stencil vector is projected only once.
+constexpr int kNPark = 36;
+constexpr int kNThreadSlots = kNBack + (WB_SWEEP_PARK ? kNPark : 0);
 
 // |lambda_s| of the interface state, s = 0..6 (u-cf, u-ca, u-cs, u, u+cs,
 // u+ca, u+cf)
@@ -434,6 +442,31 @@ __device__ __forceinline__ void project_ae(const Eig<T>& e, const T (&x)[7], T (
     o[2] = t1 - t2;
 }
 
+// all seven fields at once: the fast/slow group into o4, Alfven/entropy into
+// o3 (the shared terms dv1, dv2, P formed once)
+template <class T>
+__device__ __forceinline__ void project_all(const Eig<T>& e, const T (&x)[7], T (&o4)[4], T (&o3)[3]) {
+    const T du = x[1] - e.u * x[0];
+    const T dv1 = x[2] - e.v1 * x[0];
+    const T dv2 = x[3] - e.v2 * x[0];
+    const T P = x[6] + e.hv2 * x[0] - e.u * x[1] - e.v1 * x[2] - e.v2 * x[3]
+              - e.b1 * x[4] - e.b2 * x[5];
+    const T vpar = e.be1 * dv1 + e.be2 * dv2;
+    const T bpar = e.be1 * x[4] + e.be2 * x[5];
+    const T tf1 = e.Af * du + e.Bf * vpar, tf2 = e.Cf * bpar + e.Df * P;
+    const T ts1 = e.As * du + e.Bs * vpar, ts2 = e.Cs * bpar + e.Ds * P;
+    o4[0] = tf2 - tf1;
+    o4[1] = ts2 - ts1;
+    o4[2] = ts2 + ts1;
+    o4[3] = tf2 + tf1;
+    const T vperp = e.be1 * dv2 - e.be2 * dv1;
+    const T bperp = e.be1 * x[5] - e.be2 * x[4];
+    const T t1 = e.Aa * vperp, t2 = e.Ba * bperp;
+    o3[0] = t1 + t2;
+    o3[1] = x[0] - e.Ee * P;
+    o3[2] = t1 - t2;
+}
+
 // single field pair projections (fields processed two at a time keep the
 // projected stencil small): G = 0 fast-/fast+ (s = 0, 6), 1 slow-/slow+
 // (s = 2, 4), 2 Alfven-/Alfven+ (s = 1, 5), 3 entropy (s = 3).
@@ -473,7 +506,7 @@ __device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const in
     return al;
 }
 
-template <class T, class Wt>
+template <class T, class Wt, bool PARK = false>
 __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc, const int (&id)[6],
                                                T gamma, T* __restrict__ bp, int bstride, Wt& wt,
                                                T (&out)[7]) {
@@ -523,6 +556,46 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         }
     }
 #else
+    if constexpr (PARK) {
+        // 3. each stencil vector projected once onto all seven fields; the
+        // Alfven/entropy values wait in this thread's shared-memory slots
+        T* park = bp + kNBack * bstride;
+        T w[4][6], g[4][6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            T x[7], o4[4], o3[3];
+            load7(sm, nc, SU, id[m], x);
+            project_all(e, x, o4, o3);
+#pragma unroll
+            for (int f = 0; f < 4; f++) w[f][m] = o4[f];
+#pragma unroll
+            for (int f = 0; f < 3; f++) park[(f * 6 + m) * bstride] = o3[f];
+            load7(sm, nc, SF, id[m], x);
+            project_all(e, x, o4, o3);
+#pragma unroll
+            for (int f = 0; f < 4; f++) g[f][m] = o4[f];
+#pragma unroll
+            for (int f = 0; f < 3; f++) park[((3 + f) * 6 + m) * bstride] = o3[f];
+        }
+        // 4-5. fast and slow fields
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+            const int s = 2 * f;
+            corr[s] = wt.corr(s, w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
+        }
+        // 4-5. Alfven and entropy fields
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            T wa[6], ga[6];
+#pragma unroll
+            for (int m = 0; m < 6; m++) {
+                wa[m] = park[(f * 6 + m) * bstride];
+                ga[m] = park[((3 + f) * 6 + m) * bstride];
+            }
+            const int s = 2 * f + 1;
+            corr[s] = wt.corr(s, wa, ga, lf_speed(sm, nc, id, s, lam_avg(e, s)));
+        }
+    } else {
     // 3-5. fast and slow fields
     {
         T w[4][6], g[4][6];
@@ -564,6 +637,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
             const int s = 2 * f + 1;
             corr[s] = wt.corr(s, w[f], g[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
         }
+    }
     }
 #endif
     // 6. back-projection: sum_s r_s corr_s in primitive variables, then dU/dW,
@@ -710,7 +784,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
     T F[7];
     T* bp = sm + kNSlot * NCMAX + tid;      // this thread's back-projection slots
     JsWeights<T, Z> js;
-    interface_flux<T>(sm, NC, id, T(A.gamma), bp, kSweepNT, js, F);
+    interface_flux<T, JsWeights<T, Z>, WB_SWEEP_PARK != 0>(sm, NC, id, T(A.gamma), bp, kSweepNT, js, F);
 
     // rotate back and store at the lower face of cell ia
     int i, j, k;
@@ -778,7 +852,7 @@ __global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel_fi
 
 template <class T, int AXIS>
 constexpr size_t smem_bytes_fixed() {
-    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNBack * kSweepNT);
+    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNThreadSlots * kSweepNT);
 }
 
 template <class T, int AXIS>
@@ -789,7 +863,7 @@ constexpr size_t smem_bytes() {
 
 template <class T, int AXIS>
 constexpr size_t smem_bytes_persistent() {
-    return sizeof(T) * (kNSlot * max_nc(AXIS) + kNBack * kSweepNT);
+    return sizeof(T) * (kNSlot * max_nc(AXIS) + kNThreadSlots * kSweepNT);
 }
 
 }  // namespace
