@@ -126,6 +126,11 @@ int wb_init_grid(const wb_grid_desc *d, const double *U0, const double *b0,
  * synchronising call, pageable ones are read before the call returns. */
 int wb_set_state(wb_grid *g, const double *U, const double *b);
 
+/* The same in FP32 host arrays, for grids that hold FP32 (WB_FP32,
+ * WB_FP32_LEARNED): half the bytes to move, no rounding (the state is FP32).
+ * Errors: WB_EINVAL (null argument, an FP64 grid), WB_ECUDA. */
+int wb_set_state_f32(wb_grid *g, const float *U, const float *b);
+
 /* Advance nsteps steps of fixed size dt > 0 (Sec. 2.1 scheme; SSP-RK3 or
  * RK4 per the descriptor).  Asynchronous on the grid's stream. */
 int wb_step(wb_grid *g, double dt, int nsteps);
@@ -168,6 +173,11 @@ int wb_div_b(wb_grid *g, double out[2]);
 /* Copy the state to host arrays of the wb_init_grid layout (FP64).
  * Either pointer may be NULL to skip it.  Synchronises. */
 int wb_get_state(wb_grid *g, double *U_out, double *b_out);
+
+/* wb_get_state in FP32 host arrays for grids that hold FP32 (exact).
+ * Synchronises.  Errors: WB_EINVAL (null grid, an FP64 grid), WB_ECUDA,
+ * WB_ENONFINITE as wb_get_state. */
+int wb_get_state_f32(wb_grid *g, float *U_out, float *b_out);
 
 /* Wait for the grid's stream; reports a non-finite state seen by an earlier
  * asynchronous CFL step. */

@@ -305,11 +305,11 @@ int upload(wb_grid* g, const double* U, const double* b) {
     WB_CK(cudaMemcpyAsync(g->d_io + 8 * N, b, sizeof(double) * 3 * N, cudaMemcpyHostToDevice,
                           g->stream));
     if (g->precision == WB_FP64)
-        WB_CK(wb::launch_import<double>(g->d_io, g->d_io + 8 * N, static_cast<double*>(g->un),
-                                        g->d_blocks, g->d_patches, N, g->nblocks, g->stream));
+        WB_CK((wb::launch_import<double, double>(g->d_io, g->d_io + 8 * N, static_cast<double*>(g->un),
+                                        g->d_blocks, g->d_patches, N, g->nblocks, g->stream)));
     else
-        WB_CK(wb::launch_import<float>(g->d_io, g->d_io + 8 * N, static_cast<float*>(g->un),
-                                       g->d_blocks, g->d_patches, N, g->nblocks, g->stream));
+        WB_CK((wb::launch_import<float, double>(g->d_io, g->d_io + 8 * N, static_cast<float*>(g->un),
+                                       g->d_blocks, g->d_patches, N, g->nblocks, g->stream)));
     return WB_OK;
 }
 
@@ -826,6 +826,38 @@ int wb_conserved_totals(wb_grid* g, double out[8]) {
     return WB_OK;
 }
 
+int wb_set_state_f32(wb_grid* g, const float* U, const float* b) {
+    g_err.clear();
+    if (!g || !U || !b) return fail(WB_EINVAL, "null argument");
+    if (g->precision == WB_FP64) return fail(WB_EINVAL, "set_state_f32: the grid holds FP64");
+    WB_CK(cudaSetDevice(g->device));
+    const long long N = g->N;
+    float* io = reinterpret_cast<float*>(g->d_io);
+    WB_CK(cudaMemcpyAsync(io, U, sizeof(float) * 8 * N, cudaMemcpyHostToDevice, g->stream));
+    WB_CK(cudaMemcpyAsync(io + 8 * N, b, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, g->stream));
+    WB_CK((wb::launch_import<float, float>(io, io + 8 * N, static_cast<float*>(g->un), g->d_blocks,
+                                          g->d_patches, N, g->nblocks, g->stream)));
+    return WB_OK;
+}
+
+int wb_get_state_f32(wb_grid* g, float* U_out, float* b_out) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (g->precision == WB_FP64) return fail(WB_EINVAL, "get_state_f32: the grid holds FP64");
+    WB_CK(cudaSetDevice(g->device));
+    const long long N = g->N;
+    float* io = reinterpret_cast<float*>(g->d_io);
+    float* dU = U_out ? io : nullptr;
+    float* db = b_out ? io + 8 * N : nullptr;
+    WB_CK((wb::launch_export<float, float>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
+                                          g->d_patches, g->d_links, N, g->nblocks, g->stream)));
+    if (U_out)
+        WB_CK(cudaMemcpyAsync(U_out, dU, sizeof(float) * 8 * N, cudaMemcpyDeviceToHost, g->stream));
+    if (b_out)
+        WB_CK(cudaMemcpyAsync(b_out, db, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, g->stream));
+    return check_flag(g);
+}
+
 int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
     g_err.clear();
     if (!g) return fail(WB_EINVAL, "null grid");
@@ -834,11 +866,11 @@ int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
     double* dU = U_out ? g->d_io : nullptr;
     double* db = b_out ? g->d_io + 8 * N : nullptr;
     if (g->precision == WB_FP64)
-        WB_CK(wb::launch_export<double>(static_cast<const double*>(g->un), dU, db, g->d_blocks,
-                                        g->d_patches, g->d_links, N, g->nblocks, g->stream));
+        WB_CK((wb::launch_export<double, double>(static_cast<const double*>(g->un), dU, db, g->d_blocks,
+                                        g->d_patches, g->d_links, N, g->nblocks, g->stream)));
     else
-        WB_CK(wb::launch_export<float>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
-                                       g->d_patches, g->d_links, N, g->nblocks, g->stream));
+        WB_CK((wb::launch_export<float, double>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
+                                       g->d_patches, g->d_links, N, g->nblocks, g->stream)));
     if (U_out)
         WB_CK(cudaMemcpyAsync(U_out, dU, sizeof(double) * 8 * N, cudaMemcpyDeviceToHost, g->stream));
     if (b_out)

@@ -176,16 +176,16 @@ cudaError_t launch_totals(const T* state, const PatchDev* patches, int npatch,
                           long long ncells, double* partial, int npartial,
                           double dV, double* out, cudaStream_t s);
 
-template <class T>
-cudaError_t launch_import(const double* U, const double* b, T* state,
+template <class T, class H>
+cudaError_t launch_import(const H* U, const H* b, T* state,
                           const CellBlock* blocks, const PatchDev* patches,
                           long long ncells, int nblocks, cudaStream_t s);
 template <class T>
 cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* blocks,
                                const PatchDev* patches, long long ncells, int nblocks,
                                cudaStream_t s);
-template <class T>
-cudaError_t launch_export(const T* state, double* U, double* b,
+template <class T, class H>
+cudaError_t launch_export(const T* state, H* U, H* b,
                           const CellBlock* blocks, const PatchDev* patches, const int* links,
                           long long ncells, int nblocks, cudaStream_t s);
 

@@ -212,11 +212,12 @@ totals_pass2(const double* __restrict__ partial, int npartial, double dV, double
     }
 }
 
-// ABI layout (FP64): U[patch][8][cells] with (rho, mx, my, mz, Bx, By, Bz, E),
-// b[patch][3][cells]; state layout: field-major over all patches.
-template <class T>
+// ABI layout (FP64, or FP32 for the FP32 entry points, type H): U[patch][8][cells]
+// with (rho, mx, my, mz, Bx, By, Bz, E), b[patch][3][cells]; state layout:
+// field-major over all patches.
+template <class T, class H>
 __global__ void __launch_bounds__(kCellBlock)
-import_kernel(const double* __restrict__ U, const double* __restrict__ b, T* __restrict__ q,
+import_kernel(const H* __restrict__ U, const H* __restrict__ b, T* __restrict__ q,
               const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
               long long N) {
     const CellBlock cb = blocks[blockIdx.x];
@@ -225,8 +226,8 @@ import_kernel(const double* __restrict__ U, const double* __restrict__ b, T* __r
     const int local = cb.y + threadIdx.x;
     if (local >= np) return;
     const long long c = P.off + local;
-    const double* u = U + 8 * P.off + local;
-    const double* bb = b + 3 * P.off + local;
+    const H* u = U + 8 * P.off + local;
+    const H* bb = b + 3 * P.off + local;
     q[c] = T(u[0]);
     q[N + c] = T(u[np]);
     q[2 * N + c] = T(u[2 * np]);
@@ -237,9 +238,9 @@ import_kernel(const double* __restrict__ U, const double* __restrict__ b, T* __r
     q[7 * N + c] = T(bb[2 * np]);
 }
 
-template <class T, bool LINKED>
+template <class T, class H, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock)
-export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restrict__ b,
+export_kernel(const T* __restrict__ q, H* __restrict__ U, H* __restrict__ b,
               const CellBlock* __restrict__ blocks, const PatchDev* __restrict__ patches,
               const int* __restrict__ links, long long N) {
     const CellBlock cb = blocks[blockIdx.x];
@@ -257,21 +258,21 @@ export_kernel(const T* __restrict__ q, double* __restrict__ U, double* __restric
     const long long cy = upper<LINKED>(patches, links, cb.x, P, i, j + 1, k);
     const long long cz = upper<LINKED>(patches, links, cb.x, P, i, j, k + 1);
     if (U) {
-        double* u = U + 8 * P.off + local;
-        u[0] = double(q[c]);
-        u[np] = double(q[N + c]);
-        u[2 * np] = double(q[2 * N + c]);
-        u[3 * np] = double(q[3 * N + c]);
-        u[4 * np] = 0.5 * (double(q[5 * N + c]) + double(q[5 * N + cx]));
-        u[5 * np] = 0.5 * (double(q[6 * N + c]) + double(q[6 * N + cy]));
-        u[6 * np] = 0.5 * (double(q[7 * N + c]) + double(q[7 * N + cz]));
-        u[7 * np] = double(q[4 * N + c]);
+        H* u = U + 8 * P.off + local;
+        u[0] = H(double(q[c]));
+        u[np] = H(double(q[N + c]));
+        u[2 * np] = H(double(q[2 * N + c]));
+        u[3 * np] = H(double(q[3 * N + c]));
+        u[4 * np] = H(0.5 * (double(q[5 * N + c]) + double(q[5 * N + cx])));
+        u[5 * np] = H(0.5 * (double(q[6 * N + c]) + double(q[6 * N + cy])));
+        u[6 * np] = H(0.5 * (double(q[7 * N + c]) + double(q[7 * N + cz])));
+        u[7 * np] = H(double(q[4 * N + c]));
     }
     if (b) {
-        double* o = b + 3 * P.off + local;
-        o[0] = double(q[5 * N + c]);
-        o[np] = double(q[6 * N + c]);
-        o[2 * np] = double(q[7 * N + c]);
+        H* o = b + 3 * P.off + local;
+        o[0] = H(double(q[5 * N + c]));
+        o[np] = H(double(q[6 * N + c]));
+        o[2 * np] = H(double(q[7 * N + c]));
     }
 }
 
@@ -363,21 +364,21 @@ cudaError_t launch_totals(const T* state, const PatchDev*, int, long long ncells
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_import(const double* U, const double* b, T* state, const CellBlock* blocks,
+template <class T, class H>
+cudaError_t launch_import(const H* U, const H* b, T* state, const CellBlock* blocks,
                           const PatchDev* patches, long long ncells, int nblocks, cudaStream_t s) {
-    import_kernel<T><<<nblocks, kCellBlock, 0, s>>>(U, b, state, blocks, patches, ncells);
+    import_kernel<T, H><<<nblocks, kCellBlock, 0, s>>>(U, b, state, blocks, patches, ncells);
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock* blocks,
+template <class T, class H>
+cudaError_t launch_export(const T* state, H* U, H* b, const CellBlock* blocks,
                           const PatchDev* patches, const int* links, long long ncells, int nblocks,
                           cudaStream_t s) {
     if (links)
-        export_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
+        export_kernel<T, H, true><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
     else
-        export_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
+        export_kernel<T, H, false><<<nblocks, kCellBlock, 0, s>>>(state, U, b, blocks, patches, links, ncells);
     return cudaGetLastError();
 }
 
@@ -390,14 +391,19 @@ cudaError_t launch_export(const T* state, double* U, double* b, const CellBlock*
                                         unsigned long long*, unsigned int*, cudaStream_t);    \
     template cudaError_t launch_totals<T>(const T*, const PatchDev*, int, long long, double*, \
                                           int, double, double*, cudaStream_t);                \
-    template cudaError_t launch_import<T>(const double*, const double*, T*, const CellBlock*, \
-                                          const PatchDev*, long long, int, cudaStream_t);     \
-    template cudaError_t launch_export<T>(const T*, double*, double*, const CellBlock*,       \
-                                          const PatchDev*, const int*, long long, int,        \
-                                          cudaStream_t);                                      \
+    template cudaError_t launch_import<T, double>(const double*, const double*, T*,          \
+                                                  const CellBlock*, const PatchDev*, long long, \
+                                                  int, cudaStream_t);                          \
+    template cudaError_t launch_export<T, double>(const T*, double*, double*, const CellBlock*, \
+                                                  const PatchDev*, const int*, long long, int,  \
+                                                  cudaStream_t);                                \
     template cudaError_t launch_export_flux<T>(const T*, double*, const CellBlock*,           \
                                                const PatchDev*, long long, int, cudaStream_t);
 WB_INST(float)
+template cudaError_t launch_import<float, float>(const float*, const float*, float*, const CellBlock*,
+                                                 const PatchDev*, long long, int, cudaStream_t);
+template cudaError_t launch_export<float, float>(const float*, float*, float*, const CellBlock*,
+                                                 const PatchDev*, const int*, long long, int, cudaStream_t);
 WB_INST(double)
 #undef WB_INST
 

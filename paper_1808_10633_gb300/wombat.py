@@ -28,7 +28,8 @@ EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt"
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
            "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune",
-           "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals")
+           "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals",
+           "wb_set_state_f32", "wb_get_state_f32")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
@@ -89,6 +90,8 @@ def load() -> ctypes.CDLL:
     L.wb_learned_stats.argtypes = [vp, vp, i]
     L.wb_div_b.argtypes = [vp, dp]
     L.wb_set_step_totals.argtypes = [vp, i]
+    L.wb_set_state_f32.argtypes = [vp, vp, vp]
+    L.wb_get_state_f32.argtypes = [vp, vp, vp]
     L.wb_step_totals.argtypes = [vp, dp]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
@@ -107,13 +110,20 @@ def _check(rc: int):
         raise WombatError(rc, load().wb_last_error().decode())
 
 
-def _ptr(a) -> int:
-    """Host pointer of a C-contiguous float64 numpy array or a pinned torch tensor."""
+def _ptr(a, fp32: bool = False) -> int:
+    """Host pointer of a C-contiguous float64 (fp32: float32) numpy array or
+    pinned torch tensor."""
     if isinstance(a, np.ndarray):
-        assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+        want = np.float32 if fp32 else np.float64
+        assert a.dtype == want and a.flags.c_contiguous, f"need C-contiguous {np.dtype(want).name}"
         return a.ctypes.data
-    assert str(a.dtype) == "torch.float64" and a.is_contiguous() and not a.is_cuda
+    want = "torch.float32" if fp32 else "torch.float64"
+    assert str(a.dtype) == want and a.is_contiguous() and not a.is_cuda, f"need a host {want} tensor"
     return a.data_ptr()
+
+
+def _is_fp32(a) -> bool:
+    return str(getattr(a, "dtype", "")) in ("float32", "torch.float32")
 
 
 class Grid:
@@ -150,9 +160,9 @@ class Grid:
         _check(L.wb_init_grid(ctypes.byref(desc), _ptr(U), _ptr(b), st, ctypes.byref(h)))
         self._h = h
 
-    def _host(self, a, nf):
+    def _host(self, a, nf, dtype=np.float64):
         if isinstance(a, np.ndarray):
-            a = np.ascontiguousarray(a, dtype=np.float64)
+            a = np.ascontiguousarray(a, dtype=dtype)
             assert a.size == nf * self.ncells, (a.shape, nf, self.ncells)
         return a
 
@@ -183,7 +193,12 @@ class Grid:
 
     # -- calls -------------------------------------------------------------
     def set_state(self, U, b):
-        _check(self._lib.wb_set_state(self._h, _ptr(self._host(U, 8)), _ptr(self._host(b, 3))))
+        """Replace the state; float32 arrays (FP32 grids) take the FP32 entry point."""
+        if _is_fp32(U) and _is_fp32(b):
+            _check(self._lib.wb_set_state_f32(self._h, _ptr(self._host(U, 8, np.float32), True),
+                                              _ptr(self._host(b, 3, np.float32), True)))
+        else:
+            _check(self._lib.wb_set_state(self._h, _ptr(self._host(U, 8)), _ptr(self._host(b, 3))))
 
     def step(self, dt: float, nsteps: int = 1):
         _check(self._lib.wb_step(self._h, float(dt), int(nsteps)))
@@ -228,11 +243,15 @@ class Grid:
         _check(self._lib.wb_div_b(self._h, out))
         return float(out[0]), float(out[1])
 
-    def get_state(self, U_out=None, b_out=None):
-        """Returns (U, b) as flat float64 arrays (or fills the given buffers)."""
-        U = np.empty(8 * self.ncells) if U_out is None else U_out
-        b = np.empty(3 * self.ncells) if b_out is None else b_out
-        _check(self._lib.wb_get_state(self._h, _ptr(U), _ptr(b)))
+    def get_state(self, U_out=None, b_out=None, dtype=np.float64):
+        """Returns (U, b) as flat float64 (or float32) arrays, or fills the
+        given buffers; float32 buffers take the FP32 entry point."""
+        U = np.empty(8 * self.ncells, dtype=dtype) if U_out is None else U_out
+        b = np.empty(3 * self.ncells, dtype=dtype) if b_out is None else b_out
+        if _is_fp32(U) and _is_fp32(b):
+            _check(self._lib.wb_get_state_f32(self._h, _ptr(U, True), _ptr(b, True)))
+        else:
+            _check(self._lib.wb_get_state(self._h, _ptr(U), _ptr(b)))
         return U, b
 
     def get_state_single(self):

@@ -90,3 +90,27 @@ def test_step_totals_overlap(wb, precision):
         g1.step_totals()
     g1.close()
     g2.close()
+
+
+def test_fp32_state_entry_points(wb):
+    """wb_set_state_f32 / wb_get_state_f32 move an FP32 grid's state without
+    rounding: they agree bit for bit with the FP64 entry points, and a
+    restart through them continues bit for bit; FP64 grids refuse them."""
+    st = I.turbulence(24, seed=16)
+    g = wb.Grid.from_state(st, precision="fp32")
+    g.step_cfl(0.4, 2)
+    U64, b64 = g.get_state()
+    U32, b32 = g.get_state(dtype=np.float32)
+    assert U32.dtype == np.float32 and np.array_equal(U32.astype(np.float64), U64)
+    assert np.array_equal(b32.astype(np.float64), b64)
+    h = wb.Grid.from_state(st, precision="fp32")
+    h.set_state(U32, b32)
+    g.step_cfl(0.4, 2)
+    h.step_cfl(0.4, 2)
+    assert np.array_equal(g.get_state()[0], h.get_state()[0])
+    g.close()
+    h.close()
+    g = wb.Grid.from_state(st, precision="fp64")
+    with pytest.raises(wb.WombatError):
+        g.get_state(dtype=np.float32)
+    g.close()
