@@ -362,6 +362,7 @@ def run_native(args, rank, world, local):
         "fp64": None if g64 is None else
                 {"value": value64, "unit": UNIT, "ms_per_step": secs64 * 1e3 / k64, "steps": k64,
                  "kernel_ms_per_step": {k: v / k64 for k, v in kms64.items()}, "roofline": rf64},
+        "speedup_fp32_over_fp64": (value / value64) if g64 is not None else None,
         "fp32_vs_fp64_after_steps": args.l1_steps if l1 else 0,
         "fp32_error_vs_fp64": l1,
         "alu_peak_tflops": {"fp32": peak32, "fp64": peak64},
@@ -477,6 +478,30 @@ def run_large(args, world):
             "generate_s": t_gen}
 
 
+def bf16_peak_tflops():
+    """Measured dense BF16 tensor peak of this GPU (sustained, for a kernel
+    inside a long step) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured (MEASURED_PEAKS.json, sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (1.7 PFLOP/s sustained)"
+
+
+def learned_roofline(n, cls, ms_launch, mlp_flops, peak32):
+    """Roofline time of one learned sweep launch: the Jiang-Shu part of the
+    sweep at the FP32 FMA peak plus the networks at the BF16 tensor peak
+    (additive), against the measured launch time."""
+    iface, staged = sweep_units(n)
+    alu_flops = iface * SWEEP_FLOPS_PER_INTERFACE + staged[cls] * SWEEP_FLOPS_PER_STAGED_CELL
+    bf16, src = bf16_peak_tflops()
+    t_roof = alu_flops / (peak32 * 1e12) + mlp_flops / (bf16 * 1e12)
+    return {"bound": "alu+tensor", "ms_per_launch": round(ms_launch, 4),
+            "ms_at_peaks": round(t_roof * 1e3, 4), "frac": round(t_roof * 1e3 / ms_launch, 4),
+            "fp32_peak_tflops": round(peak32, 3), "bf16_peak_tflops": bf16, "bf16_peak_source": src}
+
+
 def _l1(U, ref):
     names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E"]
     U = U.reshape(8, -1)
@@ -524,6 +549,7 @@ def run_learned(args, st, world, peak32):
                      "steps": 1500, "harvest_s": t_h, "train_s": t_t,
                      "loss_first": float(hist[:20].mean()), "loss_last": float(hist[-20:].mean())},
            "sweep_mlp_tflops": mlp_flops / (ms_l * 1e-3) / 1e12,
+           "roofline": learned_roofline(n, cls, ms_l, mlp_flops, peak32),
            "detector_fire_rate": fired / max(decisions, 1), "weight_decisions": decisions}
     if args.l1_steps > 0:
         nst = max(1, args.l1_steps // 2)
@@ -664,10 +690,18 @@ def main():
     build.build()
     res = run_native(args, rank, world, local)
     if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
         v, s, el, cores = oracle_sample(args.cpu_seconds, args.ref_size, args.cfl)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{s} SSP-RK3 steps of a {args.ref_size}^3 periodic turbulence "
                                          f"sample of the same generator, {el:.1f} s wall"}
+        # the same oracle on one host core (a 32^3 sample, a few seconds)
+        oracle.set_num_threads(1)
+        v1, s1, el1, _ = oracle_sample(min(5.0, args.cpu_seconds), 32, args.cfl)
+        oracle.set_num_threads(cores)
+        res["cpu_baseline"]["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                              "sample": f"{s1} steps of a 32^3 sample, {el1:.1f} s wall"}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -63,6 +63,7 @@ def lib():
         L.orc_totals.argtypes = [G, _dp, _dp]
         L.orc_div_b.argtypes = [G, _dp, _dp, _dp, _dp]
         L.orc_num_threads.restype = i
+        L.orc_set_num_threads.argtypes = [i]
         _lib = L
     return _lib
 
@@ -257,6 +258,10 @@ def div_b(g: Grid, bx, by, bz):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(int(n))
 
 
 def library_path() -> str:

@@ -33,6 +33,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads the oracle's loops use from now on (timing only; every cell's
+ * arithmetic is the same with any count). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static long wrapi(long i, long n)
 {
     long r = i % n;

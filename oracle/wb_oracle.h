@@ -74,6 +74,7 @@ void   orc_totals(const orc_grid *g, const double *U, double out[8]);
 void   orc_div_b(const orc_grid *g, const double *bx, const double *by,
                  const double *bz, double *div);
 int    orc_num_threads(void);
+void   orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
