@@ -149,13 +149,15 @@ def linear_params():
     return pack(W1, b1, W2, b2, W3, b3)
 
 
-def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5):
+def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5, margins=None):
     """Eq. FWENO flux at i+1/2 (rotated frame, stencil cells i-2..i+3, 6x8)
     with the Jiang-Shu weights replaced by the network's (params: 7 x 1379)
     wherever neither detector fires: the jump detector on the side's four
     differences, or a pressure ratio max p / min p > 1 + pjump over the six
     cells (then every field falls back to Jiang-Shu).  Same steps as the
-    oracle's orc_interface_flux otherwise."""
+    oracle's orc_interface_flux otherwise.  With a list `margins`, the
+    smallest relative distance of any detector input from its threshold is
+    appended to it (how far the decisions are from flipping)."""
     import oracle as O
 
     Us = np.asarray(Us, dtype=np.float64).reshape(6, 8)
@@ -171,6 +173,7 @@ def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5):
     lam, RU, LU, _ = O.eigen(0.5 * (W[2] + W[3]), gamma)
     p = W[:, 7]
     pfire = p.max() > (1.0 + pjump) * p.min()
+    margin = abs(p.max() - (1.0 + pjump) * p.min()) / ((1.0 + pjump) * p.min())
     corr = np.empty(7)
     for s in range(7):
         alpha = max(abs(lam[s]), np.abs(lk[:, s]).max())
@@ -185,6 +188,9 @@ def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5):
         Dm = dm[[4, 3, 2, 1]]
         out = []
         for D, v in ((Dp, gp), (Dm, gm[::-1])):
+            a = np.abs(D)
+            thr = kappa * (a.sum() - a.max()) / 3.0
+            margin = min(margin, abs(a.max() - thr) / (thr + 1e-300))
             if pfire or detector(D, kappa):
                 out.append(O.phi_n(*D))
             else:
@@ -196,4 +202,6 @@ def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5):
         q = SYS[f]
         Fh[q] = (-F[1][q] + 7 * F[2][q] + 7 * F[3][q] - F[4][q]) / 12.0 + RU[f] @ corr
     Fh[4] = 0.0
+    if margins is not None:
+        margins.append(margin)
     return Fh

@@ -23,3 +23,48 @@ def oracle_face_flux(orc, st, axis, i, j, k):
     out[5] = Fh[5]
     out[6] = Fh[6]
     return out
+
+
+def bf16(a):
+    """Round float32 values to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def learned_params_as_run(params):
+    """The network parameters as the tensor-core sweep uses them: weights
+    (and the first layer's bias, fed as a weight) rounded to BF16, the hidden
+    and output biases kept FP32."""
+    from oracle import learned as Lr
+
+    p64 = np.asarray(params, np.float64).reshape(7, Lr.NPARAM)
+    P = bf16(params).reshape(7, Lr.NPARAM).copy()
+    o = 32 * 6
+    P[:, o:o + 32] = bf16(p64[:, o:o + 32])
+    o2 = o + 32 + 32 * 32
+    P[:, o2:o2 + 32] = p64[:, o2:o2 + 32]
+    P[:, -3:] = p64[:, -3:]
+    return P
+
+
+def oracle_face_flux_learned(st, axis, i, j, k, P, kappa, pjump, margins=None):
+    """Learned-weight eq. FWENO flux through the lower face of cell (i, j, k)
+    (library component order), from the FP64 reference network."""
+    from oracle import learned as Lr
+
+    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
+    perm = [0, 1 + n, 1 + t1, 1 + t2, 4 + n, 4 + t1, 4 + t2, 7]
+    dims = st.dims
+    Us = np.empty((6, 8))
+    for m in range(6):
+        q = [i, j, k]
+        q[axis] = (q[axis] + m - 3) % dims[axis]
+        Us[m] = st.U[perm, q[2], q[1], q[0]]
+    Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump, margins)
+    r = np.empty(7)
+    r[0] = Fh[0]
+    for gq in range(3):
+        r[1 + gq] = Fh[perm.index(1 + gq)]
+    r[4], r[5], r[6] = Fh[7], Fh[5], Fh[6]
+    return r

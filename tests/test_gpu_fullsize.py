@@ -114,3 +114,46 @@ def test_fullsize_4096_patches_sampled(orc, wb):
             report.append((p, kind, s.dims, float(l1), float(max(mass + flux))))
             assert l1 <= 1e-3 and max(mass + flux) <= 1e-6, report[-1]
     print("4096 patches, sampled patches:", report)
+
+
+def test_fullsize_learned_256_blasts_sampled(orc, wb):
+    """The learned-weight leg's workload (256^3 turbulence + 64 blasts, the
+    network trained by the library's own kernels, the bench's detector
+    thresholds): sampled interface fluxes against the FP64 reference network
+    on the same BF16-rounded weights.  Interfaces whose detector inputs lie
+    within 2 % of a threshold are left out (FP32 and FP64 may decide them
+    differently); the rest must agree to the BF16 tolerance of the
+    random-network parity test."""
+    from paper_1808_10633_gb300 import learned as Ln
+    from sampling import learned_params_as_run, oracle_face_flux_learned
+
+    rec = Ln.harvest(I.turbulence(64, seed=1808), 20000, seed=5)
+    params, _ = Ln.train(rec, steps=1500, batch=4096, lr=2e-3, lam=1e-3, seed=6)
+    P = learned_params_as_run(params)
+    st = I.add_blasts(I.turbulence(256, seed=1808), seed=1808, nblast=64)
+    g = wb.Grid.from_state(st, precision="learned")
+    g.set_mlp(params, 4.0, 0.5)
+    rng = np.random.default_rng(256)
+    nx, ny, nz = st.dims
+    kept, worst = 0, 0.0
+    for axis in range(3):
+        F = g.face_fluxes(axis)
+        idx = rng.integers(0, [nx, ny, nz], size=(60, 3))
+        got, ref = [], []
+        for (i, j, k) in idx:
+            margins = []
+            r = oracle_face_flux_learned(st, axis, i, j, k, P, 4.0, 0.5, margins)
+            if margins[0] < 2e-2:
+                continue
+            got.append(F[:, (k * ny + j) * nx + i])
+            ref.append(r)
+        del F
+        got, ref = np.array(got), np.array(ref)
+        kept += len(got)
+        scale = np.maximum(np.abs(ref).max(axis=0), 1e-3 * np.abs(ref).max())
+        err = (np.abs(got - ref) / scale).max()
+        worst = max(worst, err)
+        assert err < 5e-3, (axis, err)
+    g.close()
+    assert kept >= 120, kept
+    print("learned 256^3 + blasts: %d sampled interfaces, worst relative error %.2e" % (kept, worst))
