@@ -406,7 +406,7 @@ def run_patches(args, world):
             "ms_per_step_cost_model_tiles": tot0 / args.steps,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
-                            "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]},
+                            "columns": list(wombat.TILE_CANDIDATES)},
             "generate_s": t_gen}
 
 
@@ -436,7 +436,7 @@ def run_linked(args, st, world):
             "ms_per_step": secs * 1e3 / args.steps, "ms_per_step_cost_model_tiles": tot0 / args.steps,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "autotune_ms": {"x": tune[0].tolist(), "y": tune[1].tolist(), "z": tune[2].tolist(),
-                            "columns": ["per-patch model", "shape 0", "shape 1", "shape 2"]}}
+                            "columns": list(wombat.TILE_CANDIDATES)}}
 
 
 def run_large(args, world):

@@ -196,14 +196,25 @@ int wb_face_fluxes(wb_grid *g, int axis, double *F_out);
  * axis times 256/TA pencils; each axis has WB_NTILE_SHAPE shapes (default
  * first).  At wb_init_grid every patch gets the shape that needs the fewest
  * thread slots for its sizes (a cost model: ragged tiles at patch edges idle
- * threads).  wb_autotune measures, for each axis, one sweep of the current
- * state with the cost-model tiles and with each fixed shape (CUDA events,
- * second of two launches), and keeps the fastest table.  ms_out (host,
- * 3 * (WB_NTILE_SHAPE + 1), may be NULL): the times, per axis [model,
- * shape 0, shape 1, shape 2].  Not for WB_FP32_LEARNED grids.
- * Synchronises. */
+ * threads); that table runs as one persistent launch per axis whose blocks
+ * take tiles of any shape from a work counter.  wb_autotune measures, for
+ * each axis, one sweep of the current state with WB_NTILE_CANDIDATE tables
+ * (CUDA events, mean of the second and third of three launches): the
+ * cost-model table, each fixed shape everywhere, and the cost-model table
+ * ordered by shape (a launch per shape, one tile per block), and keeps the
+ * fastest.  ms_out (host, 3 * WB_NTILE_CANDIDATE, may be NULL): the times,
+ * per axis [model, shape 0, shape 1, shape 2, model by shape].  Not for
+ * WB_FP32_LEARNED grids.  Synchronises. */
 #define WB_NTILE_SHAPE 3
+#define WB_NTILE_CANDIDATE (WB_NTILE_SHAPE + 2)
 int wb_autotune(wb_grid *g, double *ms_out);
+
+/* Installs wb_autotune's candidate table `candidate` (0 <= candidate <
+ * WB_NTILE_CANDIDATE, the order of ms_out) on all three axes without timing
+ * it; WB_EINVAL outside that range or on a WB_FP32_LEARNED grid.  Every
+ * candidate gives the same fluxes: the tiles only regroup the interfaces.
+ * Synchronises. */
+int wb_set_tiles(wb_grid *g, int candidate);
 
 /* Kernel classes timed by wb_step_profiled. */
 enum {

@@ -13,6 +13,7 @@
 #include "../../include/wombat_gb300.h"
 #include "wb_internal.h"
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -93,7 +94,8 @@ struct wb_grid {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double kappa = 4.0, pjump = 0.5;
     int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
-    int tile_uniform[3] = {0, 0, 0};      // 1: the axis' tiles all use shape 0
+    int tile_split[3][3] = {};            // per axis: tiles of each shape of a table sorted
+                                          // by shape, or all 0 (wb::SweepArgs::split)
     wb::PatchDev* d_patches = nullptr;
     std::vector<wb::PatchDev> h_patches;
     int* d_links = nullptr;               // 27 per patch (wb::locate) or nullptr
@@ -117,6 +119,30 @@ struct wb_grid {
 };
 
 namespace {
+
+constexpr int kNTileCandidate = WB_NTILE_CANDIDATE;   // tile tables wb_autotune times per axis
+static_assert(WB_NTILE_SHAPE == wb::kNTileShape, "tile shape count");
+
+// Tiles of each shape when the table is sorted by shape (then each shape
+// runs as its own fixed-shape launch), else all 0.
+void tile_split(const std::vector<wb::Tile>& t, int split[3]) {
+    split[0] = split[1] = split[2] = 0;
+    int prev = 0;
+    for (const wb::Tile& x : t) {
+        const int sh = (int)((unsigned)x.x >> 24);
+        if (sh < prev || sh >= wb::kNTileShape) {
+            split[0] = split[1] = split[2] = 0;
+            return;
+        }
+        split[sh]++;
+        prev = sh;
+    }
+}
+
+template <class T>
+void set_split(wb::SweepArgs<T>& a, const int split[3]) {
+    for (int i = 0; i < 3; i++) a.split[i] = split[i];
+}
 
 template <class T>
 int enqueue_stages(wb_grid* g, Prof* pf) {
@@ -142,7 +168,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             a.ncells = N;
             a.gamma = g->gamma;
             a.zweights = g->weights;
-            a.uniform_shape0 = g->tile_uniform[axis];
+            set_split(a, g->tile_split[axis]);
             a.lstats = g->d_lstats;
             a.queue = g->d_queue + axis;
             a.flag = g->d_flag;
@@ -334,7 +360,8 @@ void release(wb_grid* g) {
 
 // Sweep tiles of `axis` for every patch.  policy >= 0: that tile shape
 // everywhere; policy < 0: per patch the shape needing the fewest thread slots
-// (ragged tiles at the patch edges idle threads), ties to the lower shape.
+// (ragged tiles at the patch edges idle threads), ties to the lower shape;
+// policy -2 then orders the table by shape (a fixed-shape launch per shape).
 // The shape goes into the top byte of the tile's patch field.
 std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
     std::vector<wb::Tile> out;
@@ -375,6 +402,10 @@ std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
                     for (int x0 = 0; x0 < P.nx; x0 += tp) out.push_back(wb::Tile{px, z0, x0, y});
         }
     }
+    if (policy == -2)
+        std::stable_sort(out.begin(), out.end(), [](const wb::Tile& a, const wb::Tile& b) {
+            return ((unsigned)a.x >> 24) < ((unsigned)b.x >> 24);
+        });
     return out;
 }
 
@@ -434,12 +465,6 @@ int check_links(const std::vector<wb::PatchDev>& P, const int* L) {
 }
 
 // 1 when every tile uses shape 0 (then one tile per block, no dispatch).
-int tiles_uniform(const std::vector<wb::Tile>& t) {
-    for (const wb::Tile& x : t)
-        if ((unsigned)x.x >> 24) return 0;
-    return 1;
-}
-
 template <class P>
 int dmalloc(wb_grid* g, P** p, size_t bytes) {
     WB_CK(cudaMalloc(reinterpret_cast<void**>(p), bytes));
@@ -461,7 +486,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     a.ncells = N;
     a.gamma = g->gamma;
     a.zweights = g->weights;
-    a.uniform_shape0 = g->tile_uniform[axis];
+    set_split(a, g->tile_split[axis]);
     a.flag = g->d_flag;
     if constexpr (sizeof(T) == 4) {
         if (g->precision == WB_FP32_LEARNED) {
@@ -484,7 +509,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
 }
 
 template <class T>
-int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, int uniform, float* ms) {
+int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, const int split[3], float* ms) {
     wb::SweepArgs<T> a;
     a.src = static_cast<const T*>(g->un);
     a.flux = static_cast<T*>(g->flux) + (long long)axis * wb::kNFlux * g->N;
@@ -495,7 +520,7 @@ int time_sweep(wb_grid* g, int axis, const wb::Tile* tiles, int ntiles, int unif
     a.ncells = g->N;
     a.gamma = g->gamma;
     a.zweights = g->weights;
-    a.uniform_shape0 = uniform;
+    set_split(a, split);
     a.queue = g->d_queue + axis;
     a.flag = g->d_flag;
     cudaEvent_t e0, e1;
@@ -604,7 +629,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     for (int a = 0; a < 3; a++) {
         if (tiles[a].size() > 0x7fffffffULL) return bail(fail(WB_EINVAL, "grid too large"));
         g->ntiles[a] = (int)tiles[a].size();
-        g->tile_uniform[a] = tiles_uniform(tiles[a]);
+        tile_split(tiles[a], g->tile_split[a]);
     }
     g->nblocks = (int)blocks.size();
     // vector blocks: periodic patches whose x extent is a multiple of the width
@@ -946,6 +971,34 @@ int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
     return WB_OK;
 }
 
+namespace {
+
+// build_tiles policy of wb_autotune's candidate table c: 0 the per-patch
+// model (one persistent launch), 1..3 each fixed shape, 4 the per-patch
+// model ordered by shape (a launch per shape)
+int candidate_policy(int c) { return c == 0 ? -1 : (c <= wb::kNTileShape ? c - 1 : -2); }
+
+// Builds and uploads the tile table of `axis` for `policy` (synchronous).
+int install_tiles(wb_grid* g, int axis, int policy) {
+    std::vector<wb::Tile> t = build_tiles(g, axis, policy);
+    if ((int)t.size() != g->ntiles[axis]) {
+        cudaFree(g->d_tiles[axis]);
+        g->d_tiles[axis] = nullptr;
+        WB_CK(cudaMalloc(&g->d_tiles[axis], sizeof(wb::Tile) * t.size()));
+        g->ntiles[axis] = (int)t.size();
+    }
+    WB_CK(cudaMemcpy(g->d_tiles[axis], t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice));
+    g->tile_policy[axis] = policy;
+    tile_split(t, g->tile_split[axis]);
+    if (g->graph) {              // tile tables changed: capture again
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    return WB_OK;
+}
+
+}  // namespace
+
 int wb_autotune(wb_grid* g, double* ms_out) {
     g_err.clear();
     if (!g) return fail(WB_EINVAL, "null grid");
@@ -954,9 +1007,11 @@ int wb_autotune(wb_grid* g, double* ms_out) {
     WB_CK(cudaStreamSynchronize(g->stream));
     for (int axis = 0; axis < 3; axis++) {
         float best_ms = -1.f;
-        int best = -2;
-        for (int c = 0; c <= wb::kNTileShape; c++) {
-            const int policy = c == 0 ? -1 : c - 1;     // 0: per-patch model, then each fixed shape
+        int best = -1;
+        for (int c = 0; c < kNTileCandidate; c++) {
+            // 0: per-patch model (one persistent launch), 1..3: each fixed
+            // shape, 4: the per-patch model sorted by shape (a launch per shape)
+            const int policy = candidate_policy(c);
             std::vector<wb::Tile> t = build_tiles(g, axis, policy);
             wb::Tile* d = nullptr;
             WB_CK(cudaMalloc(&d, sizeof(wb::Tile) * t.size()));
@@ -964,29 +1019,33 @@ int wb_autotune(wb_grid* g, double* ms_out) {
             float ms = 0.f;
             if (cudaMemcpy(d, t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
                 rc = fail(WB_ECUDA, "autotune: tile upload failed");
-            const int uni = tiles_uniform(t);
+            int split[3];
+            tile_split(t, split);
             if (rc == WB_OK)
-                rc = g->precision == WB_FP64 ? time_sweep<double>(g, axis, d, (int)t.size(), uni, &ms)
-                                             : time_sweep<float>(g, axis, d, (int)t.size(), uni, &ms);
+                rc = g->precision == WB_FP64 ? time_sweep<double>(g, axis, d, (int)t.size(), split, &ms)
+                                             : time_sweep<float>(g, axis, d, (int)t.size(), split, &ms);
             cudaFree(d);
             if (rc != WB_OK) return rc;
-            if (ms_out) ms_out[axis * (wb::kNTileShape + 1) + c] = ms;
+            if (ms_out) ms_out[axis * kNTileCandidate + c] = ms;
             if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = policy; }
         }
-        std::vector<wb::Tile> t = build_tiles(g, axis, best);
-        if ((int)t.size() != g->ntiles[axis]) {
-            cudaFree(g->d_tiles[axis]);
-            g->d_tiles[axis] = nullptr;
-            WB_CK(cudaMalloc(&g->d_tiles[axis], sizeof(wb::Tile) * t.size()));
-            g->ntiles[axis] = (int)t.size();
-        }
-        WB_CK(cudaMemcpy(g->d_tiles[axis], t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice));
-        g->tile_policy[axis] = best;
-        g->tile_uniform[axis] = tiles_uniform(t);
+        const int rc = install_tiles(g, axis, best);
+        if (rc != WB_OK) return rc;
     }
-    if (g->graph) {              // tile tables changed: capture again
-        cudaGraphExecDestroy(g->graph);
-        g->graph = nullptr;
+    return WB_OK;
+}
+
+int wb_set_tiles(wb_grid* g, int candidate) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (g->precision == WB_FP32_LEARNED) return fail(WB_EINVAL, "set_tiles: learned grids use the default tiles");
+    if (candidate < 0 || candidate >= kNTileCandidate)
+        return fail(WB_EINVAL, "set_tiles: candidate %d outside [0, %d)", candidate, kNTileCandidate);
+    WB_CK(cudaSetDevice(g->device));
+    WB_CK(cudaStreamSynchronize(g->stream));
+    for (int axis = 0; axis < 3; axis++) {
+        const int rc = install_tiles(g, axis, candidate_policy(candidate));
+        if (rc != WB_OK) return rc;
     }
     return WB_OK;
 }

@@ -99,7 +99,9 @@ struct SweepArgs {
     int zweights = 0;              // 1: WENO-Z weights instead of Jiang-Shu
     unsigned long long* lstats = nullptr;   // learned sweep: detector firings, decisions
     int* queue = nullptr;          // persistent sweep: tile counter of this launch (or fixed stride)
-    int uniform_shape0 = 0;        // 1: every tile uses shape 0 (one tile per block)
+    int split[3] = {0, 0, 0};      // tiles of shape 0, 1, 2 of a table sorted by shape
+                                   // (one fixed launch per shape, a tile per block);
+                                   // all 0: the persistent runtime-shape launch
     unsigned int* flag = nullptr;  // status word (bounds-checked builds)
 };
 

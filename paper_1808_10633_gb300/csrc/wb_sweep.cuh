@@ -837,22 +837,23 @@ __global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel(co
     }
 }
 
-// One tile per block, default shape, Jiang-Shu weights: the launch for tile
-// tables that use shape 0 throughout (a single grid, or patches tuned to it).
-template <class T, int AXIS>
+// One tile per block of one shape S, Jiang-Shu weights: the launch for tile
+// tables that use shape 0 throughout (a single grid, or patches tuned to
+// it), and for each shape's range of a table sorted by shape.
+template <class T, int AXIS, int S = 0>
 __global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel_fixed(const SweepArgs<T> A) {
-    constexpr int NC0 = nc_of(shape_ta(AXIS, 0));
+    constexpr int NC0 = nc_of(shape_ta(AXIS, S));
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     Tile tile = A.tiles[blockIdx.x];
     tile.x &= 0xffffff;
     const PatchDev P = A.patches[tile.x];
-    tile_body<T, AXIS, shape_ta(AXIS, 0), NC0, false>(A, tile, P, sm, threadIdx.x);
+    tile_body<T, AXIS, shape_ta(AXIS, S), NC0, false>(A, tile, P, sm, threadIdx.x);
 }
 
-template <class T, int AXIS>
+template <class T, int AXIS, int S = 0>
 constexpr size_t smem_bytes_fixed() {
-    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, 0)) + kNThreadSlots * kSweepNT);
+    return sizeof(T) * (kNSlot * nc_of(shape_ta(AXIS, S)) + kNThreadSlots * kSweepNT);
 }
 
 template <class T, int AXIS>
@@ -912,15 +913,14 @@ cudaError_t prepare_sweep_kernels() {
     e = cudaFuncSetAttribute(sweep_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes_persistent<T, 2>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes_fixed<T, 0>());
+#define WB_FIXED_ATTR(AX, S)                                                                    \
+    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, AX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem_bytes_fixed<T, AX, S>());                                 \
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes_fixed<T, 1>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel_fixed<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes_fixed<T, 2>());
-    if (e != cudaSuccess) return e;
+    WB_FIXED_ATTR(0, 0) WB_FIXED_ATTR(0, 1) WB_FIXED_ATTR(0, 2)
+    WB_FIXED_ATTR(1, 0) WB_FIXED_ATTR(1, 1) WB_FIXED_ATTR(1, 2)
+    WB_FIXED_ATTR(2, 0) WB_FIXED_ATTR(2, 1) WB_FIXED_ATTR(2, 2)
+#undef WB_FIXED_ATTR
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -928,13 +928,24 @@ cudaError_t prepare_sweep_kernels() {
     return cudaGetLastError();
 }
 
+template <class T, int S>
+void launch_fixed_shape(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
+    if (axis == 0) sweep_kernel_fixed<T, 0, S><<<ntiles, kSweepNT, smem_bytes_fixed<T, 0, S>(), s>>>(a);
+    else if (axis == 1) sweep_kernel_fixed<T, 1, S><<<ntiles, kSweepNT, smem_bytes_fixed<T, 1, S>(), s>>>(a);
+    else sweep_kernel_fixed<T, 2, S><<<ntiles, kSweepNT, smem_bytes_fixed<T, 2, S>(), s>>>(a);
+}
+
 template <class T>
 cudaError_t launch_sweep(int axis, const SweepArgs<T>& a, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (a.uniform_shape0 && !a.zweights) {
-        if (axis == 0) sweep_kernel_fixed<T, 0><<<ntiles, kSweepNT, smem_bytes_fixed<T, 0>(), s>>>(a);
-        else if (axis == 1) sweep_kernel_fixed<T, 1><<<ntiles, kSweepNT, smem_bytes_fixed<T, 1>(), s>>>(a);
-        else sweep_kernel_fixed<T, 2><<<ntiles, kSweepNT, smem_bytes_fixed<T, 2>(), s>>>(a);
+    if ((a.split[0] | a.split[1] | a.split[2]) && !a.zweights) {
+        // a table sorted by shape: one launch of the fixed kernel per shape
+        SweepArgs<T> b = a;
+        if (a.split[0]) launch_fixed_shape<T, 0>(axis, b, a.split[0], s);
+        b.tiles = a.tiles + a.split[0];
+        if (a.split[1]) launch_fixed_shape<T, 1>(axis, b, a.split[1], s);
+        b.tiles = a.tiles + a.split[0] + a.split[1];
+        if (a.split[2]) launch_fixed_shape<T, 2>(axis, b, a.split[2], s);
         return cudaGetLastError();
     }
     const int grid = PersistGrid<T>::g[axis] > 0 ? PersistGrid<T>::g[axis] : 152;

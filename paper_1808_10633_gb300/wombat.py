@@ -27,10 +27,11 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune",
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune", "wb_set_tiles",
            "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals",
            "wb_set_state_f32", "wb_get_state_f32")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
+TILE_CANDIDATES = ("per-patch model", "shape 0", "shape 1", "shape 2", "per-patch model by shape")
 KERNEL_CLASSES = ("sweep_x", "sweep_y", "sweep_z", "update", "cfl", "dt", "totals", "emf")
 
 
@@ -87,6 +88,7 @@ def load() -> ctypes.CDLL:
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
     L.wb_set_mlp.argtypes = [vp, vp, d, d]
     L.wb_autotune.argtypes = [vp, vp]
+    L.wb_set_tiles.argtypes = [vp, ctypes.c_int]
     L.wb_learned_stats.argtypes = [vp, vp, i]
     L.wb_div_b.argtypes = [vp, dp]
     L.wb_set_step_totals.argtypes = [vp, i]
@@ -268,11 +270,17 @@ class Grid:
         return out.reshape(7, self.ncells)
 
     def autotune(self) -> np.ndarray:
-        """Measure and keep the fastest sweep tile tables; times (3, 4) in ms
-        per axis for [per-patch model, shape 0, shape 1, shape 2]."""
-        ms = np.empty(12)
+        """Measure and keep the fastest sweep tile tables; times (3, 5) in ms
+        per axis for TILE_CANDIDATES (per-patch model, shape 0, shape 1,
+        shape 2, per-patch model ordered by shape)."""
+        ms = np.empty(3 * len(TILE_CANDIDATES))
         _check(self._lib.wb_autotune(self._h, ms.ctypes.data))
-        return ms.reshape(3, 4)
+        return ms.reshape(3, len(TILE_CANDIDATES))
+
+    def set_tiles(self, candidate: int):
+        """Install one of the autotuner's tile tables (an index into
+        TILE_CANDIDATES) without timing it."""
+        _check(self._lib.wb_set_tiles(self._h, int(candidate)))
 
     def set_mlp(self, params, kappa: float = 4.0, pjump: float = 0.5):
         """Install the learned-weight networks (7 x 1379 floats)."""

@@ -80,7 +80,7 @@ def test_fullsize_4096_patches_sampled(orc, wb):
     sts = I.patch_batch(4096, seed=1808)
     g = wb.Grid.from_patches(sts, precision="fp32")
     ms = g.autotune()
-    assert ms.shape == (3, 4) and np.all(ms > 0)
+    assert ms.shape == (3, 5) and np.all(ms > 0)
     dt = g.cfl_dt(0.4)
     g.step(dt, 1)
     U, b = g.get_state()

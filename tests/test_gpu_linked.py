@@ -68,7 +68,7 @@ def test_bricks_rk4_mean_emf_cfl_and_autotune(wb, world):
     g2 = wb.Grid.from_bricks(world, CUTS, **kw)
     assert g1.cfl_dt(0.4) == g2.cfl_dt(0.4)
     ms = g2.autotune()
-    assert ms.shape == (3, 4)
+    assert ms.shape == (3, 5)
     for g in (g1, g2):
         g.step_cfl(0.4, 3)
     U1, b1 = g1.get_state()

@@ -236,9 +236,38 @@ def test_patch_tile_shapes_and_autotune_match_oracle(orc, wb):
     g.set_state(np.concatenate([s.U.ravel() for s in sts]),
                 np.concatenate([np.stack([s.bx, s.by, s.bz]).ravel() for s in sts]))
     ms = g.autotune()
-    assert ms.shape == (3, 4) and np.all(ms > 0)
+    assert ms.shape == (3, 5) and np.all(ms > 0)
     g.step(dt, 2)
     check(g)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_tile_table_gives_the_same_fluxes(wb, prec):
+    """Uneven patches whose cost-model shapes differ per patch: each of the
+    autotuner's candidate tables (one persistent launch, one fixed shape
+    everywhere, a fixed-shape launch per shape) regroups the same
+    interfaces, so the fluxes of every axis agree with the first table to
+    rounding, and a step from the same state lands on the same state."""
+    sts = I.patch_batch(9, seed=23, lo=12, hi=40)
+    g = wb.Grid.from_patches(sts, precision=prec)
+    U0, b0 = g.get_state()
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    ref = None
+    for c in range(len(wb.TILE_CANDIDATES)):
+        g.set_tiles(c)
+        g.set_state(U0, b0)
+        F = np.stack([g.face_fluxes(axis) for axis in range(3)])
+        g.step(2e-4, 1)
+        U1 = g.get_state()[0]
+        if ref is None:
+            ref = (F, U1)
+            continue
+        scale = np.abs(ref[0]).max(axis=2, keepdims=True) + 1e-30
+        assert (np.abs(F - ref[0]) / scale).max() <= tol, c
+        assert np.abs(U1 - ref[1]).max() <= tol * np.abs(ref[1]).max(), c
+    with pytest.raises(RuntimeError):
+        g.set_tiles(len(wb.TILE_CANDIDATES))
     g.close()
 
 
