@@ -378,8 +378,8 @@ def run_native(args, rank, world, local):
 
 def run_patches(args, world):
     """Independent periodic patches, edges log-uniform in [16, 64] (aspect
-    <= 2), each a rotated Brio-Wu tube or a turbulence state; FP32, one
-    persistent launch per sweep axis with per-patch tile shapes, autotuned."""
+    <= 2), each a rotated Brio-Wu tube or a turbulence state; FP32, per-patch
+    tile shapes (a launch per shape and sweep axis), then autotuned."""
     import torch
 
     from paper_1808_10633_gb300 import inputs, wombat

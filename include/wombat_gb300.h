@@ -193,11 +193,14 @@ int wb_sync(wb_grid *g);
 int wb_face_fluxes(wb_grid *g, int axis, double *F_out);
 
 /* Autotuner of the sweep tiles.  A sweep tile is TA interfaces along the
- * axis times 256/TA pencils; each axis has WB_NTILE_SHAPE shapes (default
- * first).  At wb_init_grid every patch gets the shape that needs the fewest
- * thread slots for its sizes (a cost model: ragged tiles at patch edges idle
- * threads); that table runs as one persistent launch per axis whose blocks
- * take tiles of any shape from a work counter.  wb_autotune measures, for
+ * axis times 128/TA pencils (one per thread of a block); each axis has
+ * WB_NTILE_SHAPE shapes (default first).  At wb_init_grid every patch gets
+ * the shape that needs the fewest thread slots for its sizes (a cost model:
+ * ragged tiles at patch edges idle threads) and the table is ordered by
+ * shape, so that each shape runs as its own launch of one tile per block.
+ * The same table unordered runs as one persistent launch per axis whose
+ * blocks take tiles of any shape from a work counter (the WENO-Z sweeps
+ * always run that way).  wb_autotune measures, for
  * each axis, one sweep of the current state with WB_NTILE_CANDIDATE tables
  * (CUDA events, mean of the second and third of three launches): the
  * cost-model table, each fixed shape everywhere, and the cost-model table

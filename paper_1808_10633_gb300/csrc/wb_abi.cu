@@ -93,7 +93,7 @@ struct wb_grid {
     cudaStream_t side = nullptr;          // stream the per-step totals run on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double kappa = 4.0, pjump = 0.5;
-    int tile_policy[3] = {-1, -1, -1};    // -1 per-patch model, else fixed shape
+    int tile_policy[3] = {-2, -2, -2};    // build_tiles policy of each axis' table
     int tile_split[3][3] = {};            // per axis: tiles of each shape of a table sorted
                                           // by shape, or all 0 (wb::SweepArgs::split)
     wb::PatchDev* d_patches = nullptr;
@@ -620,7 +620,7 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     // tiles and cell blocks
     std::vector<wb::Tile> tiles[3];
     std::vector<wb::CellBlock> blocks;
-    for (int a = 0; a < 3; a++) tiles[a] = build_tiles(g, a, g->precision == WB_FP32_LEARNED ? 0 : -1);
+    for (int a = 0; a < 3; a++) tiles[a] = build_tiles(g, a, g->precision == WB_FP32_LEARNED ? 0 : -2);
     for (int p = 0; p < g->npatch; p++) {
         const wb::PatchDev& P = g->h_patches[p];
         const long long np = (long long)P.nx * P.ny * P.nz;

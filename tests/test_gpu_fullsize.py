@@ -5,8 +5,7 @@ sampled outputs that the oracle computes one at a time.
   FP64 islands: eq. FWENO fluxes at random interfaces and at interfaces
   across blast edges, against the oracle's single-interface flux.
 - 4096 periodic patches with edges log-uniform in [16, 64], each a rotated
-  Brio-Wu tube or a turbulence state, FP32 in one persistent launch per axis
-  with autotuned tile shapes: one CFL step, then whole patches against the
+  Brio-Wu tube or a turbulence state, FP32 with autotuned tile tables: one CFL step, then whole patches against the
   oracle's step of the same patch.
 
 FP32 tolerances.  A flux sample's components mix through the characteristic

@@ -206,8 +206,9 @@ def test_fullsize_256_sampled_interfaces(orc, wb, prec, tol):
 
 def test_patch_tile_shapes_and_autotune_match_oracle(orc, wb):
     """Patches whose sizes make the cost model pick each of the three x-sweep
-    tile shapes inside one persistent launch; then the autotuner swaps tile
-    tables; both agree with the oracle patch by patch."""
+    tile shapes (a launch per shape); the same table as one persistent
+    launch; then the autotuner's pick: all agree with the oracle patch by
+    patch."""
     rng = np.random.default_rng(17)
     dims = [(16, 16, 8), (64, 4, 6), (32, 8, 8), (12, 20, 9)]
     sts = [I.perturbed(*d, seed=40 + n, jump=True) for n, d in enumerate(dims)]
@@ -230,11 +231,16 @@ def test_patch_tile_shapes_and_autotune_match_oracle(orc, wb):
             oU += 8 * n
             ob += 3 * n
 
+    U0 = np.concatenate([s.U.ravel() for s in sts])
+    b0 = np.concatenate([np.stack([s.bx, s.by, s.bz]).ravel() for s in sts])
     g = wb.Grid.from_patches(sts, precision="fp64")
     g.step(dt, 2)
     check(g)
-    g.set_state(np.concatenate([s.U.ravel() for s in sts]),
-                np.concatenate([np.stack([s.bx, s.by, s.bz]).ravel() for s in sts]))
+    g.set_tiles(0)
+    g.set_state(U0, b0)
+    g.step(dt, 2)
+    check(g)
+    g.set_state(U0, b0)
     ms = g.autotune()
     assert ms.shape == (3, 5) and np.all(ms > 0)
     g.step(dt, 2)
