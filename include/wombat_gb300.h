@@ -122,8 +122,12 @@ int wb_init_grid(const wb_grid_desc *d, const double *U0, const double *b0,
                  void *cuda_stream, wb_grid **out);
 
 /* Replace the state with host arrays of the wb_init_grid layout.  Ordered on
- * the grid's stream; pinned host arrays must stay valid until the next
- * synchronising call, pageable ones are read before the call returns. */
+ * the grid's stream.  Page-locked arrays mapped at the same address on the
+ * grid's device (cudaHostAlloc memory, e.g. pinned torch tensors) are read
+ * in place by the import kernel over the host link, with no staging copy;
+ * they must stay valid until the next synchronising call.  Pageable arrays
+ * are copied through a device staging buffer and read before the call
+ * returns.  The same holds for every state entry point below. */
 int wb_set_state(wb_grid *g, const double *U, const double *b);
 
 /* The same in FP32 host arrays, for grids that hold FP32 (WB_FP32,
@@ -171,7 +175,8 @@ int wb_step_totals(wb_grid *g, double out[8]);
 int wb_div_b(wb_grid *g, double out[2]);
 
 /* Copy the state to host arrays of the wb_init_grid layout (FP64).
- * Either pointer may be NULL to skip it.  Synchronises. */
+ * Either pointer may be NULL to skip it.  Mapped page-locked arrays are
+ * written in place by the export kernel.  Synchronises. */
 int wb_get_state(wb_grid *g, double *U_out, double *b_out);
 
 /* wb_get_state in FP32 host arrays for grids that hold FP32 (exact).

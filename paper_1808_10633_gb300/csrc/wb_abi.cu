@@ -325,8 +325,35 @@ int check_flag(wb_grid* g) {
     return WB_OK;
 }
 
+// The address under which the grid's device reads or writes a host array in
+// place: page-locked memory mapped at the same address (cudaHostAlloc
+// memory under unified addressing, e.g. a pinned torch tensor), allocated
+// while that device was current.  nullptr for pageable memory, which is
+// staged through a copy instead.
+template <class P>
+P* mapped(const wb_grid* g, P* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer != static_cast<const void*>(host) ||
+        a.device != g->device)
+        return nullptr;
+    return host;
+}
+
 int upload(wb_grid* g, const double* U, const double* b) {
     const long long N = g->N;
+    if (mapped(g, U) && mapped(g, b)) {      // the import kernel reads the host arrays in place
+        if (g->precision == WB_FP64)
+            WB_CK((wb::launch_import<double, double>(U, b, static_cast<double*>(g->un), g->d_blocks,
+                                                     g->d_patches, N, g->nblocks, g->stream)));
+        else
+            WB_CK((wb::launch_import<float, double>(U, b, static_cast<float*>(g->un), g->d_blocks,
+                                                    g->d_patches, N, g->nblocks, g->stream)));
+        return WB_OK;
+    }
     WB_CK(cudaMemcpyAsync(g->d_io, U, sizeof(double) * 8 * N, cudaMemcpyHostToDevice, g->stream));
     WB_CK(cudaMemcpyAsync(g->d_io + 8 * N, b, sizeof(double) * 3 * N, cudaMemcpyHostToDevice,
                           g->stream));
@@ -857,6 +884,11 @@ int wb_set_state_f32(wb_grid* g, const float* U, const float* b) {
     if (g->precision == WB_FP64) return fail(WB_EINVAL, "set_state_f32: the grid holds FP64");
     WB_CK(cudaSetDevice(g->device));
     const long long N = g->N;
+    if (mapped(g, U) && mapped(g, b)) {      // the import kernel reads the host arrays in place
+        WB_CK((wb::launch_import<float, float>(U, b, static_cast<float*>(g->un), g->d_blocks,
+                                              g->d_patches, N, g->nblocks, g->stream)));
+        return WB_OK;
+    }
     float* io = reinterpret_cast<float*>(g->d_io);
     WB_CK(cudaMemcpyAsync(io, U, sizeof(float) * 8 * N, cudaMemcpyHostToDevice, g->stream));
     WB_CK(cudaMemcpyAsync(io + 8 * N, b, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, g->stream));
@@ -871,6 +903,12 @@ int wb_get_state_f32(wb_grid* g, float* U_out, float* b_out) {
     if (g->precision == WB_FP64) return fail(WB_EINVAL, "get_state_f32: the grid holds FP64");
     WB_CK(cudaSetDevice(g->device));
     const long long N = g->N;
+    if ((!U_out || mapped(g, U_out)) && (!b_out || mapped(g, b_out))) {
+        // the export kernel writes the host arrays in place
+        WB_CK((wb::launch_export<float, float>(static_cast<const float*>(g->un), U_out, b_out, g->d_blocks,
+                                              g->d_patches, g->d_links, N, g->nblocks, g->stream)));
+        return check_flag(g);
+    }
     float* io = reinterpret_cast<float*>(g->d_io);
     float* dU = U_out ? io : nullptr;
     float* db = b_out ? io + 8 * N : nullptr;
@@ -888,17 +926,18 @@ int wb_get_state(wb_grid* g, double* U_out, double* b_out) {
     if (!g) return fail(WB_EINVAL, "null grid");
     WB_CK(cudaSetDevice(g->device));
     const long long N = g->N;
-    double* dU = U_out ? g->d_io : nullptr;
-    double* db = b_out ? g->d_io + 8 * N : nullptr;
+    const bool in_place = (!U_out || mapped(g, U_out)) && (!b_out || mapped(g, b_out));
+    double* dU = U_out ? (in_place ? U_out : g->d_io) : nullptr;
+    double* db = b_out ? (in_place ? b_out : g->d_io + 8 * N) : nullptr;
     if (g->precision == WB_FP64)
         WB_CK((wb::launch_export<double, double>(static_cast<const double*>(g->un), dU, db, g->d_blocks,
                                         g->d_patches, g->d_links, N, g->nblocks, g->stream)));
     else
         WB_CK((wb::launch_export<float, double>(static_cast<const float*>(g->un), dU, db, g->d_blocks,
                                        g->d_patches, g->d_links, N, g->nblocks, g->stream)));
-    if (U_out)
+    if (U_out && !in_place)
         WB_CK(cudaMemcpyAsync(U_out, dU, sizeof(double) * 8 * N, cudaMemcpyDeviceToHost, g->stream));
-    if (b_out)
+    if (b_out && !in_place)
         WB_CK(cudaMemcpyAsync(b_out, db, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, g->stream));
     return check_flag(g);
 }
