@@ -149,6 +149,31 @@ __device__ __forceinline__ T phi_n_z(T a, T b, T c, T d) {
     return a0 * r * (a - T(2) * b + c) * T(1.0 / 3.0) + (a2 * r - T(0.5)) * (b - T(2) * c + d) * T(1.0 / 6.0);
 }
 
+// phi_n_z on the (minus, plus) pair of one field, as phi_n2 does for
+// phi_n; tau5 and the three weights per lane as in phi_n_z.
+__device__ __forceinline__ float2 phi_n_z2(float2 a, float2 b, float2 c, float2 d) {
+    const float2 t0 = __ffma2_rn(b, splat2(-1.0f), a), t1 = __ffma2_rn(b, splat2(-3.0f), a);
+    const float2 is0 = __ffma2_rn(__fmul2_rn(t0, splat2(13.0f)), t0, __fmul2_rn(__fmul2_rn(t1, splat2(3.0f)), t1));
+    const float2 t2 = __ffma2_rn(c, splat2(-1.0f), b), t3 = __fadd2_rn(b, c);
+    const float2 is1 = __ffma2_rn(__fmul2_rn(t2, splat2(13.0f)), t2, __fmul2_rn(__fmul2_rn(t3, splat2(3.0f)), t3));
+    const float2 t4 = __ffma2_rn(d, splat2(-1.0f), c), t5 = __ffma2_rn(c, splat2(3.0f), __fmul2_rn(d, splat2(-1.0f)));
+    const float2 is2 = __ffma2_rn(__fmul2_rn(t4, splat2(13.0f)), t4, __fmul2_rn(__fmul2_rn(t5, splat2(3.0f)), t5));
+    const float2 dt = __ffma2_rn(is2, splat2(-1.0f), is0);
+    const float2 tau = make_float2(fabsf(dt.x), fabsf(dt.y));
+    const float2 e0 = __fadd2_rn(is0, splat2(1e-6f)), e1 = __fadd2_rn(is1, splat2(1e-6f)),
+                 e2 = __fadd2_rn(is2, splat2(1e-6f));
+    const float2 a0 = __ffma2_rn(tau, make_float2(1.0f / e0.x, 1.0f / e0.y), splat2(1.0f));
+    const float2 a1 = __fmul2_rn(__ffma2_rn(tau, make_float2(1.0f / e1.x, 1.0f / e1.y), splat2(1.0f)), splat2(6.0f));
+    const float2 a2 = __fmul2_rn(__ffma2_rn(tau, make_float2(1.0f / e2.x, 1.0f / e2.y), splat2(1.0f)), splat2(3.0f));
+    const float2 sum = __fadd2_rn(__fadd2_rn(a0, a1), a2);
+    const float2 r = make_float2(1.0f / sum.x, 1.0f / sum.y);
+    const float2 w0 = __fmul2_rn(a0, r);
+    const float2 h2 = __ffma2_rn(a2, r, splat2(-0.5f));
+    const float2 p = __ffma2_rn(b, splat2(-2.0f), __fadd2_rn(a, c));
+    const float2 q = __ffma2_rn(c, splat2(-2.0f), __fadd2_rn(b, d));
+    return __ffma2_rn(__fmul2_rn(w0, splat2(1.0f / 3.0f)), p, __fmul2_rn(__fmul2_rn(h2, splat2(1.0f / 6.0f)), q));
+}
+
 // Correction of eq. FWENO for one characteristic field:
 // -phi_N(D+_{i-3/2}, D+_{i-1/2}, D+_{i+1/2}, D+_{i+3/2})
 // +phi_N(D-_{i+5/2}, D-_{i+3/2}, D-_{i+1/2}, D-_{i-1/2}),
@@ -164,7 +189,11 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
     // gm[k] holds g-_{k+1}
     T dp0 = gp[1] - gp[0], dp1 = gp[2] - gp[1], dp2 = gp[3] - gp[2], dp3 = gp[4] - gp[3];
     T dm1 = gm[1] - gm[0], dm2 = gm[2] - gm[1], dm3 = gm[3] - gm[2], dm4 = gm[4] - gm[3];
-    if constexpr (Z) {
+    if constexpr (Z && WB_SWEEP_PACKED && sizeof(T) == 4) {
+        const float2 ph = phi_n_z2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
+                                   make_float2(dm1, dp3));
+        return ph.x - ph.y;
+    } else if constexpr (Z) {
         return phi_n_z(dm4, dm3, dm2, dm1) - phi_n_z(dp0, dp1, dp2, dp3);
     } else if constexpr (WB_SWEEP_PACKED && sizeof(T) == 4) {
         const float2 ph = phi_n2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
