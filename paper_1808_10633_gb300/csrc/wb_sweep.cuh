@@ -758,7 +758,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
 #define WB_SWEEP_TA_YZ 16
 #endif
 #ifndef WB_SWEEP_MINB_F32
-#define WB_SWEEP_MINB_F32 2
+#define WB_SWEEP_MINB_F32 2        // in 256-thread units (four 128-thread blocks)
 #endif
 // threads (= interfaces) per block of the Jiang-Shu / WENO-Z sweeps; the
 // register budget per thread is kept when it changes (blocks per SM scale)
@@ -774,7 +774,11 @@ template <> struct Shape<1> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256
 template <> struct Shape<2> { static constexpr int TA = WB_SWEEP_TA_YZ, TP = 256 / WB_SWEEP_TA_YZ; };
 
 template <class T> struct MinBlocks { static constexpr int value = 256 / kSweepNT > 1 ? 256 / kSweepNT : 1; };
+#ifdef WB_SWEEP_BLOCKS_F32      // resident blocks per SM, overriding the above
+template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_BLOCKS_F32; };
+#else
 template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB_F32 * 256 / kSweepNT; };
+#endif
 
 // Tile shapes a tile may use, per axis: TA interfaces along the axis times
 // TP = kSweepNT / TA pencils.  Shape 0 is the default; the host picks a shape per
