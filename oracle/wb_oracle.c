@@ -24,6 +24,12 @@
 #endif
 #include "wb_oracle.h"
 
+/* extended-precision accumulator of the totals (a name of its own so that
+ * the operation-counting build, count_ops.cpp, can keep it) */
+#ifndef ORC_WIDE
+#define ORC_WIDE long double
+#endif
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
@@ -720,9 +726,9 @@ void orc_totals(const orc_grid *g, const double *U, double out[8])
     long N = ncell(g);
     double dV = g->dx * g->dy * g->dz;
     for (int q = 0; q < 8; q++) {
-        long double acc = 0.0L;
-        for (long c = 0; c < N; c++) acc += (long double)U[q * N + c];
-        out[q] = (double)(acc * (long double)dV);
+        ORC_WIDE acc = 0.0L;
+        for (long c = 0; c < N; c++) acc += (ORC_WIDE)U[q * N + c];
+        out[q] = (double)(acc * (ORC_WIDE)dV);
     }
 }
 
