@@ -74,10 +74,34 @@ __device__ __forceinline__ uint32_t gelu2x(float a, float b) {
 
 // One warp, one field: omega (w0, w2) for the 64 rows of `in` (row r holds 8
 // bf16: x0..x5, 1, 0) into om[2r], om[2r+1].
-__device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const uint32_t* __restrict__ in,
+#ifndef WB_LEARNED_HOIST
+#define WB_LEARNED_HOIST 1
+#endif
+// This lane's fragment words of one field: read from shared memory at each
+// use, or (WB_LEARNED_HOIST) once into registers for all four row tiles.
+struct WordsSmem {
+    const uint32_t* W;
+    int lane;
+    __device__ __forceinline__ uint32_t operator()(int k) const { return W[k * 32 + lane]; }
+};
+struct WordsReg {
+    uint32_t w[kMlpWords];
+    __device__ __forceinline__ WordsReg(const uint32_t* W, int lane) {
+#pragma unroll
+        for (int k = 0; k < kMlpWords; k++) w[k] = W[k * 32 + lane];
+    }
+    __device__ __forceinline__ uint32_t operator()(int k) const { return w[k]; }
+};
+
+__device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const uint32_t* __restrict__ in,
                                          float* __restrict__ om, int lane) {
     const int g = lane >> 2, t = lane & 3;
-    const float* Wf = reinterpret_cast<const float*>(W);
+#if WB_LEARNED_HOIST
+    const WordsReg W(Ws, lane);
+#else
+    const WordsSmem W{Ws, lane};
+#endif
+    auto Wf = [&](int k) { return __uint_as_float(W(k)); };
 #pragma unroll 1
     for (int mt = 0; mt < 4; mt++) {
         const int r0 = 16 * mt + g, r1 = r0 + 8;
@@ -86,7 +110,7 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
             c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
-            mma_k8(c1[nt], a0, a1, W[nt * 32 + lane]);
+            mma_k8(c1[nt], a0, a1, W(nt));
         }
         uint32_t A2[2][4];
 #pragma unroll
@@ -99,12 +123,11 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
         float c2[4][4];
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
-            const float blo = Wf[(24 + 2 * nt) * 32 + lane], bhi = Wf[(25 + 2 * nt) * 32 + lane];
+            const float blo = Wf(24 + 2 * nt), bhi = Wf(25 + 2 * nt);
             c2[nt][0] = blo; c2[nt][1] = bhi; c2[nt][2] = blo; c2[nt][3] = bhi;
 #pragma unroll
             for (int kt = 0; kt < 2; kt++)
-                mma_k16(c2[nt], A2[kt], W[(4 + nt * 4 + kt * 2) * 32 + lane],
-                        W[(5 + nt * 4 + kt * 2) * 32 + lane]);
+                mma_k16(c2[nt], A2[kt], W(4 + nt * 4 + kt * 2), W(5 + nt * 4 + kt * 2));
         }
         uint32_t A3[2][4];
 #pragma unroll
@@ -114,11 +137,11 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ W, const u
             A3[kt][2] = gelu2x(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
             A3[kt][3] = gelu2x(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
         }
-        const float b3lo = Wf[32 * 32 + lane], b3hi = Wf[33 * 32 + lane];
+        const float b3lo = Wf(32), b3hi = Wf(33);
         float c3[4] = {b3lo, b3hi, b3lo, b3hi};
 #pragma unroll
         for (int kt = 0; kt < 2; kt++)
-            mma_k16(c3, A3[kt], W[(20 + kt * 2) * 32 + lane], W[(21 + kt * 2) * 32 + lane]);
+            mma_k16(c3, A3[kt], W(20 + kt * 2), W(21 + kt * 2));
         // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1
         const float z2a = __shfl_down_sync(0xffffffffu, c3[0], 1);
         const float z2b = __shfl_down_sync(0xffffffffu, c3[2], 1);
