@@ -142,21 +142,21 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
 #pragma unroll
         for (int kt = 0; kt < 2; kt++)
             mma_k16(c3, A3[kt], W(20 + kt * 2), W(21 + kt * 2));
-        // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1
+        // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1 (row
+        // r0 in c3[0..1], row r1 in c3[2..3]); lane t = 0 takes the softmax
+        // of row r0 and lane t = 1 that of row r1
         const float z2a = __shfl_down_sync(0xffffffffu, c3[0], 1);
-        const float z2b = __shfl_down_sync(0xffffffffu, c3[2], 1);
-        if (t == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const float z0 = h == 0 ? c3[0] : c3[2], z1 = h == 0 ? c3[1] : c3[3];
-                const float z2 = h == 0 ? z2a : z2b;
-                const float zm = fmaxf(z0, fmaxf(z1, z2));
-                const float e0 = __expf(z0 - zm), e1 = __expf(z1 - zm), e2 = __expf(z2 - zm);
-                const float inv = __fdividef(1.0f, e0 + e1 + e2);
-                const int r = h == 0 ? r0 : r1;
-                om[2 * r] = e0 * inv;
-                om[2 * r + 1] = e2 * inv;
-            }
+        const float z0b = __shfl_up_sync(0xffffffffu, c3[2], 1);
+        const float z1b = __shfl_up_sync(0xffffffffu, c3[3], 1);
+        if (t < 2) {
+            const float z0 = t == 0 ? c3[0] : z0b, z1 = t == 0 ? c3[1] : z1b;
+            const float z2 = t == 0 ? z2a : c3[2];
+            const float zm = fmaxf(z0, fmaxf(z1, z2));
+            const float e0 = __expf(z0 - zm), e1 = __expf(z1 - zm), e2 = __expf(z2 - zm);
+            const float inv = __fdividef(1.0f, e0 + e1 + e2);
+            const int r = t == 0 ? r0 : r1;
+            om[2 * r] = e0 * inv;
+            om[2 * r + 1] = e2 * inv;
         }
     }
 }
