@@ -4,6 +4,7 @@
 #include "wb_internal.h"
 
 #include <cfloat>
+#include <limits>
 
 namespace wb {
 namespace {
@@ -32,7 +33,10 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
            const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
            double idx, double idy, double idz, double gamma, unsigned long long* smax_bits,
            unsigned int* flag) {
-    double s = 0.0;
+    // the running maximum stays in T: the largest of FP32 values converted to
+    // FP64 once is the largest of their FP64 conversions (the conversion is
+    // exact and monotonic), and FP32 grids keep the FP64 pipe out of the loop
+    T s = T(0);
     // grid-stride over the cell blocks: one atomic per resident block, not
     // one per 256 cells (same-address atomics serialise in L2)
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
@@ -72,28 +76,35 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
                 const T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
                 sp += (fabs(v[d]) + cf) * id[d];
             }
-            double sc = double(sp);
+            T sc = sp;
             unsigned int bad = 0;
-            if (!(sc <= DBL_MAX)) bad |= 1u;             // NaN or Inf
+            if (!(sc <= std::numeric_limits<T>::max())) bad |= 1u;   // NaN or Inf
             if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
             if (bad) {
                 atomicOr(flag, bad);
-                sc = 0.0;
+                sc = T(0);
             }
-            s = fmax(s, sc);
+            s = sc > s ? sc : s;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    __shared__ double red[kCellBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const T r = __shfl_xor_sync(0xffffffffu, s, o);
+        s = r > s ? r : s;
+    }
+    __shared__ T red[kCellBlock / 32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
-        s = threadIdx.x < kCellBlock / 32 ? red[threadIdx.x] : 0.0;
+        s = threadIdx.x < kCellBlock / 32 ? red[threadIdx.x] : T(0);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-        // s >= 0: the IEEE bit patterns order like the values
-        if (threadIdx.x == 0) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(s));
+        for (int o = 16; o > 0; o >>= 1) {
+            const T r = __shfl_xor_sync(0xffffffffu, s, o);
+            s = r > s ? r : s;
+        }
+        // s >= 0: the IEEE bit patterns of its FP64 value order like the values
+        if (threadIdx.x == 0)
+            atomicMax(smax_bits, (unsigned long long)__double_as_longlong(double(s)));
     }
 }
 
