@@ -166,6 +166,33 @@ __global__ void set_dt_kernel(const unsigned long long* smax_bits, double cfl, d
 // patch the sum of the face means equals the sum over faces).  Pass 1: each
 // block reduces a fixed contiguous chunk in a fixed order; pass 2: one block
 // reduces the partials.  Same order on every call, so bitwise repeatable.
+// The FP64 value of an FP32 number, formed from its bits with integer
+// operations (IEEE 754 binary32 -> binary64 is exact: sign kept, exponent
+// rebiased by 1023 - 127, mantissa widened by 29 zero bits; subnormals
+// normalised, zero, infinities and NaN mapped to their binary64 forms).  The
+// conversion instruction would run on the FP64 pipe, which is narrow on this
+// GPU; here only the sums do.
+__device__ __forceinline__ double widen(float x) {
+    const unsigned int u = __float_as_uint(x);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned int e = (u >> 23) & 0xffu;
+    unsigned int m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) {                       // infinity or NaN
+        bits = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (e != 0u) {                   // normal
+        bits = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {                   // signed zero
+        bits = sign;
+    } else {                                // subnormal: value m 2^-149
+        const int sh = __clz(m) - 8;        // shifts that bring the top bit to bit 23
+        m = (m << sh) & 0x7fffffu;
+        bits = sign | ((unsigned long long)(897 - sh) << 52) | ((unsigned long long)m << 29);
+    }
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 template <class T>
 __global__ void __launch_bounds__(256)
 totals_pass1(const T* __restrict__ q, long long N, long long chunk, double* __restrict__ partial) {
@@ -175,7 +202,7 @@ totals_pass1(const T* __restrict__ q, long long N, long long chunk, double* __re
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long c = beg + threadIdx.x; c < end; c += 256) {
 #pragma unroll
-        for (int f = 0; f < 8; f++) acc[f] += double(q[f * N + c]);
+        for (int f = 0; f < 8; f++) acc[f] += widen(q[f * N + c]);
     }
     __shared__ double red[8][256];
 #pragma unroll

@@ -67,6 +67,31 @@ def test_runs_are_deterministic(wb, precision):
     assert np.array_equal(t1, t2) and d1 == d2
 
 
+def test_fp32_totals_widen_exactly(wb):
+    """The FP32 totals widen each value to FP64 with integer operations:
+    on values whose FP64 sums are exact in any order (subnormals, signed
+    zeros, small-mantissa normals, huge and tiny exponents) the totals equal
+    the exact sums."""
+    n = 16
+    rng = np.random.default_rng(5)
+    shape = (n, n, n)
+    ints = lambda lo, hi: rng.integers(lo, hi, size=shape).astype(np.float64)
+    U = np.zeros((8,) + shape)
+    U[0] = ints(-2 ** 20, 2 ** 20) * 2.0 ** -149             # subnormal FP32 values
+    U[1] = ints(-1000, 1000) / 1024.0
+    U[2] = np.where(rng.random(shape) < 0.5, -0.0, 2.0 ** -126 * ints(-3, 4))
+    U[3] = ints(-1000, 1000) * 2.0 ** 100
+    U[7] = ints(-2 ** 10, 2 ** 10) * 2.0 ** -140              # subnormal and tiny normal
+    b = np.stack([ints(-2 ** 22, 2 ** 22) * 2.0 ** -149, ints(-4, 5) * 1.5, np.full(shape, -0.0)])
+    assert np.array_equal(U.astype(np.float32).astype(np.float64), U)
+    g = wb.Grid([(n, n, n)], 1.0, 1.0, 1.0, U, b, precision="fp32")
+    got = g.totals()
+    want = np.array([U[0].sum(), U[1].sum(), U[2].sum(), U[3].sum(),
+                     b[0].sum(), b[1].sum(), b[2].sum(), U[7].sum()])
+    assert np.array_equal(got, want), (got, want)
+    g.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_step_totals_overlap(wb, precision):
     """Per-step totals (second stream inside the step graph) equal the
