@@ -224,12 +224,14 @@ int enqueue_cfl(wb_grid* g, Prof* pf = nullptr) {
     WB_CK(cudaMemsetAsync(g->d_smax, 0, sizeof(unsigned long long), g->stream));
     if (g->precision == WB_FP64)
         WB_CK(wb::launch_cfl<double>(static_cast<const double*>(g->un), g->d_blocks, g->d_patches, g->d_links,
-                                     g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
-                                     g->gamma, g->d_smax, g->d_flag, g->stream));
+                                     g->N, g->nblocks, g->d_vblocks, g->nvblocks, 1.0 / g->dx,
+                                     1.0 / g->dy, 1.0 / g->dz, g->gamma, g->d_smax, g->d_flag,
+                                     g->stream));
     else
         WB_CK(wb::launch_cfl<float>(static_cast<const float*>(g->un), g->d_blocks, g->d_patches, g->d_links,
-                                    g->N, g->nblocks, 1.0 / g->dx, 1.0 / g->dy, 1.0 / g->dz,
-                                    g->gamma, g->d_smax, g->d_flag, g->stream));
+                                    g->N, g->nblocks, g->d_vblocks, g->nvblocks, 1.0 / g->dx,
+                                    1.0 / g->dy, 1.0 / g->dz, g->gamma, g->d_smax, g->d_flag,
+                                    g->stream));
     return prof_end(pf, g->stream, WB_K_CFL);
 }
 

@@ -81,6 +81,52 @@ using CellBlock = int2;
 
 constexpr int kCellBlock = 256;   // cells per block of the per-cell kernels
 
+// Operations with explicit rounding (no contraction into FMAs), for values
+// that several kernels must compute to the same bits.
+namespace rn {
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+}  // namespace rn
+
+// The CFL signal rate of one cell, sum over the axes d of
+// (|v_d| + c_f,d) / dx_d with c_f,d the fast speed along d, from its rho,
+// momentum, total energy and cell-centred B (the CFL rule; the paper states
+// none).  Every operation is rounded explicitly, so the scalar and the vector
+// CFL kernels agree to the bit.  p receives the gas pressure.
+template <class T>
+__device__ __forceinline__ T cell_signal(T rho, T m0, T m1, T m2, T E, T B0, T B1, T B2, T g,
+                                         T id0, T id1, T id2, T& p) {
+    const T rinv = rn::div(T(1), rho);
+    const T v0 = rn::mul(m0, rinv), v1 = rn::mul(m1, rinv), v2 = rn::mul(m2, rinv);
+    const T bb = rn::add(rn::add(rn::mul(B0, B0), rn::mul(B1, B1)), rn::mul(B2, B2));
+    const T vv = rn::add(rn::add(rn::mul(v0, v0), rn::mul(v1, v1)), rn::mul(v2, v2));
+    const T kin = rn::mul(rn::mul(T(0.5), rho), vv);
+    p = rn::mul(rn::sub(g, T(1)), rn::sub(rn::sub(E, kin), rn::mul(T(0.5), bb)));
+    const T a2 = rn::mul(rn::mul(g, p), rinv);
+    const T sum = rn::add(a2, rn::mul(bb, rinv));
+    const T s2 = rn::mul(sum, sum), a4 = rn::mul(T(4), a2);
+    const T Bd[3] = {B0, B1, B2}, vd[3] = {v0, v1, v2}, id[3] = {id0, id1, id2};
+    T sp = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const T ca2 = rn::mul(rn::mul(Bd[d], Bd[d]), rinv);
+        T disc = rn::sub(s2, rn::mul(a4, ca2));
+        disc = disc > T(0) ? disc : T(0);
+        const T cf = rn::sqrt(rn::mul(T(0.5), rn::add(sum, rn::sqrt(disc))));
+        const T av = vd[d] < T(0) ? -vd[d] : vd[d];
+        sp = rn::add(sp, rn::mul(rn::add(av, cf), id[d]));
+    }
+    return sp;
+}
+
 // Number of state arrays: rho, mx, my, mz, E (cell) + bx, by, bz (faces).
 constexpr int kNState = 8;
 // Stored flux components per axis: rho, mx, my, mz, E, B_t1, B_t2.
@@ -163,9 +209,9 @@ cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, in
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
-                       const int* links, long long ncells, int nblocks, double idx, double idy, double idz,
-                       double gamma, unsigned long long* smax_bits, unsigned int* flag,
-                       cudaStream_t s);
+                       const int* links, long long ncells, int nblocks, const CellBlock* vblocks,
+                       int nvblocks, double idx, double idy, double idz, double gamma,
+                       unsigned long long* smax_bits, unsigned int* flag, cudaStream_t s);
 template <class T>
 cudaError_t launch_divb(const T* state, const CellBlock* blocks, const PatchDev* patches,
                         const int* links, long long ncells, int nblocks, double idx, double idy,

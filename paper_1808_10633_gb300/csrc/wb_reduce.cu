@@ -27,15 +27,56 @@ __device__ __forceinline__ long long upper(const PatchDev* __restrict__ patches,
     return P.off + ((long long)k * P.ny + j) * P.nx + i;
 }
 
+// Folds one cell's signal rate into the running maximum s (kept in T: the
+// largest of FP32 values converted to FP64 once is the largest of their FP64
+// conversions, the conversion being exact and monotonic, so FP32 grids keep
+// the FP64 pipe out of the loop); flags NaN/Inf and rho, p <= 0.
+template <class T>
+__device__ __forceinline__ void fold_signal(T& s, T rho, T m0, T m1, T m2, T E, T B0, T B1, T B2,
+                                            T g, T id0, T id1, T id2, unsigned int* flag) {
+    T p;
+    T sc = cell_signal<T>(rho, m0, m1, m2, E, B0, B1, B2, g, id0, id1, id2, p);
+    unsigned int bad = 0;
+    if (!(sc <= std::numeric_limits<T>::max())) bad |= 1u;   // NaN or Inf
+    if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
+    if (bad) {
+        atomicOr(flag, bad);
+        sc = T(0);
+    }
+    s = sc > s ? sc : s;
+}
+
+// Block maximum of s, folded into *smax_bits as an FP64 bit pattern (s >= 0,
+// so the IEEE bit patterns order like the values).
+template <class T>
+__device__ __forceinline__ void block_max_out(T s, unsigned long long* smax_bits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T r = __shfl_xor_sync(0xffffffffu, s, o);
+        s = r > s ? r : s;
+    }
+    __shared__ T red[kCellBlock / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < kCellBlock / 32 ? red[threadIdx.x] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T r = __shfl_xor_sync(0xffffffffu, s, o);
+            s = r > s ? r : s;
+        }
+        if (threadIdx.x == 0)
+            atomicMax(smax_bits, (unsigned long long)__double_as_longlong(double(s)));
+    }
+}
+
+// One thread per cell, any patches (linked ones too).
 template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock)
 cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nblocks,
            const PatchDev* __restrict__ patches, const int* __restrict__ links, long long N,
            double idx, double idy, double idz, double gamma, unsigned long long* smax_bits,
            unsigned int* flag) {
-    // the running maximum stays in T: the largest of FP32 values converted to
-    // FP64 once is the largest of their FP64 conversions (the conversion is
-    // exact and monotonic), and FP32 grids keep the FP64 pipe out of the loop
     T s = T(0);
     // grid-stride over the cell blocks: one atomic per resident block, not
     // one per 256 cells (same-address atomics serialise in L2)
@@ -53,59 +94,80 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
             const long long cx = chk(upper<LINKED>(patches, links, cb.x, P, i + 1, j, k), N, flag);
             const long long cy = chk(upper<LINKED>(patches, links, cb.x, P, i, j + 1, k), N, flag);
             const long long cz = chk(upper<LINKED>(patches, links, cb.x, P, i, j, k + 1), N, flag);
-            const T g = T(gamma);
-            const T rho = q[c];
-            const T rinv = T(1) / rho;
-            const T v[3] = {q[N + c] * rinv, q[2 * N + c] * rinv, q[3 * N + c] * rinv};
-            const T B[3] = {T(0.5) * (q[5 * N + c] + q[5 * N + cx]),
-                            T(0.5) * (q[6 * N + c] + q[6 * N + cy]),
-                            T(0.5) * (q[7 * N + c] + q[7 * N + cz])};
-            const T bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-            const T kin = T(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            const T p = (g - T(1)) * (q[4 * N + c] - kin - T(0.5) * bb);
-            const T a2 = g * p * rinv;
-            const T b2 = bb * rinv;
-            const T sum = a2 + b2;
-            const T id[3] = {T(idx), T(idy), T(idz)};
-            T sp = T(0);
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const T ca2 = B[d] * B[d] * rinv;
-                T disc = sum * sum - T(4) * a2 * ca2;
-                disc = disc > T(0) ? disc : T(0);
-                const T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
-                sp += (fabs(v[d]) + cf) * id[d];
-            }
-            T sc = sp;
-            unsigned int bad = 0;
-            if (!(sc <= std::numeric_limits<T>::max())) bad |= 1u;   // NaN or Inf
-            if (!(rho > T(0)) || !(p > T(0))) bad |= 2u;
-            if (bad) {
-                atomicOr(flag, bad);
-                sc = T(0);
-            }
-            s = sc > s ? sc : s;
+            fold_signal<T>(s, q[c], q[N + c], q[2 * N + c], q[3 * N + c], q[4 * N + c],
+                           rn::mul(T(0.5), rn::add(q[5 * N + c], q[5 * N + cx])),
+                           rn::mul(T(0.5), rn::add(q[6 * N + c], q[6 * N + cy])),
+                           rn::mul(T(0.5), rn::add(q[7 * N + c], q[7 * N + cz])), T(gamma), T(idx),
+                           T(idy), T(idz), flag);
         }
     }
+    block_max_out<T>(s, smax_bits);
+}
+
+template <class T> struct CflVec;
+template <> struct CflVec<float> { using type = float4; static constexpr int V = 4; };
+template <> struct CflVec<double> { using type = double2; static constexpr int V = 2; };
+
+template <class T, int V>
+__device__ __forceinline__ void vget(const T* __restrict__ p, T (&v)[V]) {
+    const typename CflVec<T>::type x = *reinterpret_cast<const typename CflVec<T>::type*>(p);
+    if constexpr (V == 4) { v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; }
+    else { v[0] = x.x; v[1] = x.y; }
+}
+
+// One thread per 16-byte vector of cells along x, for periodic patches whose
+// x extent is a multiple of the vector width (vector blocks of the grid):
+// four times the bytes in flight per thread, the same per-cell arithmetic.
+template <class T>
+__global__ void __launch_bounds__(kCellBlock)
+cfl_kernel_vec(const T* __restrict__ q, const CellBlock* __restrict__ vblocks, int nvblocks,
+               const PatchDev* __restrict__ patches, long long N, double idx, double idy, double idz,
+               double gamma, unsigned long long* smax_bits, unsigned int* flag) {
+    constexpr int V = CflVec<T>::V;
+    T s = T(0);
+    for (int b = blockIdx.x; b < nvblocks; b += gridDim.x) {
+        const CellBlock cb = vblocks[b];
+        const PatchDev P = patches[cb.x];
+        const int local = cb.y + threadIdx.x * V;
+        const int nxy = P.nx * P.ny;
+        if (local < nxy * P.nz) {
+            const int k = local / nxy;
+            const int rem = local - k * nxy;
+            const int j = rem / P.nx;
+            const int i = rem - j * P.nx;
+            const int ip = i + V == P.nx ? 0 : i + V;
+            const int jp = j + 1 == P.ny ? 0 : j + 1, kp = k + 1 == P.nz ? 0 : k + 1;
+            auto at = [&](int a, int bb, int cc) { return P.off + ((long long)cc * P.ny + bb) * P.nx + a; };
+            const long long c = P.off + local, cxp = at(ip, j, k), cyp = at(i, jp, k), czp = at(i, j, kp);
+#if WB_BOUNDS_CHECK
+            auto vec_ok = [&](long long a) { return a >= 0 && a + V <= N && a % V == 0; };
+            if (!(vec_ok(c) && vec_ok(cyp) && vec_ok(czp) && cxp >= 0 && cxp < N)) {
+                atomicOr(flag, kFlagBounds);
+                continue;
+            }
+#endif
+            T rho[V], m0[V], m1[V], m2[V], E[V], bx[V], by[V], bz[V], byp[V], bzp[V];
+            vget<T, V>(q + c, rho);
+            vget<T, V>(q + N + c, m0);
+            vget<T, V>(q + 2 * N + c, m1);
+            vget<T, V>(q + 3 * N + c, m2);
+            vget<T, V>(q + 4 * N + c, E);
+            vget<T, V>(q + 5 * N + c, bx);
+            vget<T, V>(q + 6 * N + c, by);
+            vget<T, V>(q + 7 * N + c, bz);
+            vget<T, V>(q + 6 * N + cyp, byp);
+            vget<T, V>(q + 7 * N + czp, bzp);
+            const T bx_next = q[5 * N + cxp];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T r = __shfl_xor_sync(0xffffffffu, s, o);
-        s = r > s ? r : s;
-    }
-    __shared__ T red[kCellBlock / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        s = threadIdx.x < kCellBlock / 32 ? red[threadIdx.x] : T(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T r = __shfl_xor_sync(0xffffffffu, s, o);
-            s = r > s ? r : s;
+            for (int v = 0; v < V; v++) {
+                const T bxu = v + 1 < V ? bx[v + 1] : bx_next;
+                fold_signal<T>(s, rho[v], m0[v], m1[v], m2[v], E[v], rn::mul(T(0.5), rn::add(bx[v], bxu)),
+                               rn::mul(T(0.5), rn::add(by[v], byp[v])), rn::mul(T(0.5), rn::add(bz[v], bzp[v])),
+                               T(gamma), T(idx), T(idy), T(idz), flag);
+            }
         }
-        // s >= 0: the IEEE bit patterns of its FP64 value order like the values
-        if (threadIdx.x == 0)
-            atomicMax(smax_bits, (unsigned long long)__double_as_longlong(double(s)));
     }
+    block_max_out<T>(s, smax_bits);
 }
 
 // Face divergence of b per cell (the quantity constrained transport keeps at
@@ -343,9 +405,9 @@ cudaError_t launch_export_flux(const T* flux, double* out, const CellBlock* bloc
 
 template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
-                       const int* links, long long ncells, int nblocks, double idx, double idy,
-                       double idz, double gamma, unsigned long long* smax_bits,
-                       unsigned int* flag, cudaStream_t s) {
+                       const int* links, long long ncells, int nblocks, const CellBlock* vblocks,
+                       int nvblocks, double idx, double idy, double idz, double gamma,
+                       unsigned long long* smax_bits, unsigned int* flag, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     static int grid_cap = 0;
     if (grid_cap == 0) {
@@ -353,6 +415,12 @@ cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         grid_cap = 8 * (nsm > 0 ? nsm : 152);      // one wave of 256-thread blocks
+    }
+    if (vblocks && nvblocks > 0 && !links) {
+        const int vgrid = nvblocks < grid_cap ? nvblocks : grid_cap;
+        cfl_kernel_vec<T><<<vgrid, kCellBlock, 0, s>>>(state, vblocks, nvblocks, patches, ncells, idx, idy,
+                                                       idz, gamma, smax_bits, flag);
+        return cudaGetLastError();
     }
     const int grid = nblocks < grid_cap ? nblocks : grid_cap;
     if (links)
@@ -422,8 +490,9 @@ cudaError_t launch_export(const T* state, H* U, H* b, const CellBlock* blocks,
 
 #define WB_INST(T)                                                                            \
     template cudaError_t launch_cfl<T>(const T*, const CellBlock*, const PatchDev*, const int*, \
-                                       long long, int, double, double, double, double,       \
-                                       unsigned long long*, unsigned int*, cudaStream_t);     \
+                                       long long, int, const CellBlock*, int, double, double, \
+                                       double, double, unsigned long long*, unsigned int*,    \
+                                       cudaStream_t);                                         \
     template cudaError_t launch_divb<T>(const T*, const CellBlock*, const PatchDev*, const int*, \
                                         long long, int, double, double, double,              \
                                         unsigned long long*, unsigned int*, cudaStream_t);    \
