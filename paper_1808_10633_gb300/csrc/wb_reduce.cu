@@ -78,6 +78,7 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
            double idx, double idy, double idz, double gamma, unsigned long long* smax_bits,
            unsigned int* flag) {
     T s = T(0);
+    const T g = T(gamma), i0 = T(idx), i1 = T(idy), i2 = T(idz);
     // grid-stride over the cell blocks: one atomic per resident block, not
     // one per 256 cells (same-address atomics serialise in L2)
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
@@ -97,8 +98,7 @@ cfl_kernel(const T* __restrict__ q, const CellBlock* __restrict__ blocks, int nb
             fold_signal<T>(s, q[c], q[N + c], q[2 * N + c], q[3 * N + c], q[4 * N + c],
                            rn::mul(T(0.5), rn::add(q[5 * N + c], q[5 * N + cx])),
                            rn::mul(T(0.5), rn::add(q[6 * N + c], q[6 * N + cy])),
-                           rn::mul(T(0.5), rn::add(q[7 * N + c], q[7 * N + cz])), T(gamma), T(idx),
-                           T(idy), T(idz), flag);
+                           rn::mul(T(0.5), rn::add(q[7 * N + c], q[7 * N + cz])), g, i0, i1, i2, flag);
         }
     }
     block_max_out<T>(s, smax_bits);
@@ -125,6 +125,7 @@ cfl_kernel_vec(const T* __restrict__ q, const CellBlock* __restrict__ vblocks, i
                double gamma, unsigned long long* smax_bits, unsigned int* flag) {
     constexpr int V = CflVec<T>::V;
     T s = T(0);
+    const T g = T(gamma), i0 = T(idx), i1 = T(idy), i2 = T(idz);
     for (int b = blockIdx.x; b < nvblocks; b += gridDim.x) {
         const CellBlock cb = vblocks[b];
         const PatchDev P = patches[cb.x];
@@ -163,7 +164,7 @@ cfl_kernel_vec(const T* __restrict__ q, const CellBlock* __restrict__ vblocks, i
                 const T bxu = v + 1 < V ? bx[v + 1] : bx_next;
                 fold_signal<T>(s, rho[v], m0[v], m1[v], m2[v], E[v], rn::mul(T(0.5), rn::add(bx[v], bxu)),
                                rn::mul(T(0.5), rn::add(by[v], byp[v])), rn::mul(T(0.5), rn::add(bz[v], bzp[v])),
-                               T(gamma), T(idx), T(idy), T(idz), flag);
+                               g, i0, i1, i2, flag);
             }
         }
     }
