@@ -25,6 +25,12 @@
 // thread on these bandwidth-bound kernels.
 #include "wb_internal.h"
 
+// FP32 grids whose per-cell kernels cannot use the vector forms run the
+// two-cells-per-thread forms (0: one cell per thread)
+#ifndef WB_UPDATE_PAIRS
+#define WB_UPDATE_PAIRS 1
+#endif
+
 namespace wb {
 namespace {
 
@@ -146,6 +152,53 @@ __global__ void __launch_bounds__(kCellBlock) emf_kernel(const UpdateArgs<T> A) 
                                 m0 ? Er[2 * N + cim] : T(0), m0 ? Er[2 * N + c] : T(0), A.emf_mode);
 }
 
+// Two cells per thread (t and t + 128 of a 256-cell block), the loads of
+// both issued before the first store; the same arithmetic as emf_kernel.
+template <class T, bool LINKED>
+__global__ void __launch_bounds__(kCellBlock / 2) emf_kernel2(const UpdateArgs<T> A) {
+    constexpr int H = kCellBlock / 2;
+    const CellBlock cb = A.blocks[blockIdx.x];
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x, A.ncells, A.flag};
+    const int nxy = G.P.nx * G.P.ny, np = nxy * G.P.nz;
+    const int local0 = cb.y + threadIdx.x;
+    if (local0 >= np) return;
+    const bool has1 = local0 + H < np;
+    const long long N = A.ncells;
+    const T* __restrict__ Fx = A.flux;
+    const T* __restrict__ Fy = A.flux + 7 * N;
+    const T* __restrict__ Fz = A.flux + 14 * N;
+    const T* __restrict__ Er = A.er;
+    const bool m0 = A.emf_mode == 0;
+    long long c[2];
+    T e[2][3];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int local = u == 1 && has1 ? local0 + H : local0;
+        const int k = local / nxy;
+        const int rem = local - k * nxy;
+        const int j = rem / G.P.nx;
+        const int i = rem - j * G.P.nx;
+        c[u] = chk(G.P.off + local, N, A.flag);
+        const long long cc = c[u];
+        const long long cim = G.at(i - 1, j, k), cjm = G.at(i, j - 1, k), ckm = G.at(i, j, k - 1);
+        e[u][0] = edge_emf(-Fy[5 * N + ckm], -Fy[5 * N + cc], Fz[6 * N + cjm], Fz[6 * N + cc],
+                           m0 ? Er[G.at(i, j - 1, k - 1)] : T(0), m0 ? Er[ckm] : T(0),
+                           m0 ? Er[cjm] : T(0), m0 ? Er[cc] : T(0), A.emf_mode);
+        e[u][1] = edge_emf(Fx[6 * N + ckm], Fx[6 * N + cc], -Fz[5 * N + cim], -Fz[5 * N + cc],
+                           m0 ? Er[N + G.at(i - 1, j, k - 1)] : T(0), m0 ? Er[N + ckm] : T(0),
+                           m0 ? Er[N + cim] : T(0), m0 ? Er[N + cc] : T(0), A.emf_mode);
+        e[u][2] = edge_emf(-Fx[5 * N + cjm], -Fx[5 * N + cc], Fy[6 * N + cim], Fy[6 * N + cc],
+                           m0 ? Er[2 * N + G.at(i - 1, j - 1, k)] : T(0), m0 ? Er[2 * N + cjm] : T(0),
+                           m0 ? Er[2 * N + cim] : T(0), m0 ? Er[2 * N + cc] : T(0), A.emf_mode);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        if (u == 1 && !has1) break;
+#pragma unroll
+        for (int d = 0; d < 3; d++) A.emf[d * N + c[u]] = e[u][d];
+    }
+}
+
 template <class T, bool LINKED>
 __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<T> A) {
     const CellBlock cb = A.blocks[blockIdx.x];
@@ -189,6 +242,77 @@ __global__ void __launch_bounds__(kCellBlock, 4) update_kernel(const UpdateArgs<
         const T out = combine_value(A.integrator, A.stage, un, uk, acc, Lq[q], dt);
         if (A.integrator == 1 && A.stage < 3) A.acc[o] = acc;
         A.dst[o] = out;
+    }
+}
+
+// Two cells per thread (cells t and t + 128 of a 256-cell block): all loads
+// of both cells are issued before the first store, so each thread keeps
+// twice the bytes in flight of update_kernel (same arithmetic, same bits).
+template <class T, bool LINKED>
+__global__ void __launch_bounds__(kCellBlock / 2, 6) update_kernel2(const UpdateArgs<T> A) {
+    constexpr int H = kCellBlock / 2;
+    const CellBlock cb = A.blocks[blockIdx.x];
+    const Geo<T, LINKED> G{A.patches[cb.x], A.patches, A.links, cb.x, A.ncells, A.flag};
+    const int nxy = G.P.nx * G.P.ny, np = nxy * G.P.nz;
+    const int local0 = cb.y + threadIdx.x;
+    if (local0 >= np) return;
+    const bool has1 = local0 + H < np;
+    const long long N = A.ncells;
+    long long c[2], cx[2], cy[2], cz[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int local = u == 1 && has1 ? local0 + H : local0;
+        const int k = local / nxy;
+        const int rem = local - k * nxy;
+        const int j = rem / G.P.nx;
+        const int i = rem - j * G.P.nx;
+        c[u] = chk(G.P.off + local, N, A.flag);
+        cx[u] = G.at(i + 1, j, k);
+        cy[u] = G.at(i, j + 1, k);
+        cz[u] = G.at(i, j, k + 1);
+    }
+    const T dt = T(*A.dt);
+    const T idx = T(A.idx), idy = T(A.idy), idz = T(A.idz);
+    const T* __restrict__ Fx = A.flux;
+    const T* __restrict__ Fy = A.flux + 7 * N;
+    const T* __restrict__ Fz = A.flux + 14 * N;
+    const T* __restrict__ Ex = A.emf;
+    const T* __restrict__ Ey = A.emf + N;
+    const T* __restrict__ Ez = A.emf + 2 * N;
+    T Lq[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            const long long o = q * N;
+            Lq[u][q] = flux_rate(Fx[o + cx[u]], Fx[o + c[u]], Fy[o + cy[u]], Fy[o + c[u]], Fz[o + cz[u]],
+                                 Fz[o + c[u]], idx, idy, idz);
+        }
+        const T ex = Ex[c[u]], ey = Ey[c[u]], ez = Ez[c[u]];
+        Lq[u][5] = face_rate(Ez[cy[u]], ez, idy, Ey[cz[u]], ey, idz);
+        Lq[u][6] = face_rate(Ex[cz[u]], ex, idz, Ez[cx[u]], ez, idx);
+        Lq[u][7] = face_rate(Ey[cx[u]], ey, idx, Ex[cy[u]], ex, idy);
+    }
+    T un[2][8], uk[2][8], acc[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const long long o = q * N + c[u];
+            un[u][q] = A.un[o];
+            uk[u][q] = A.stage > 0 && A.integrator == 0 ? A.uk[o] : T(0);
+            acc[u][q] = A.integrator == 1 && A.stage > 0 ? A.acc[o] : T(0);
+        }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        if (u == 1 && !has1) break;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const long long o = q * N + c[u];
+            const T out = combine_value(A.integrator, A.stage, un[u][q], uk[u][q], acc[u][q], Lq[u][q], dt);
+            if (A.integrator == 1 && A.stage < 3) A.acc[o] = acc[u][q];
+            A.dst[o] = out;
+        }
     }
 }
 
@@ -404,6 +528,11 @@ cudaError_t launch_emf(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
         return cudaGetLastError();
     }
     if (nblocks <= 0) return cudaSuccess;
+    if constexpr (WB_UPDATE_PAIRS && sizeof(T) == 4) {
+        if (a.links) emf_kernel2<T, true><<<nblocks, kCellBlock / 2, 0, s>>>(a);
+        else emf_kernel2<T, false><<<nblocks, kCellBlock / 2, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.links) emf_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(a);
     else emf_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(a);
     return cudaGetLastError();
@@ -418,6 +547,11 @@ cudaError_t launch_update(const UpdateArgs<T>& a, int nblocks, cudaStream_t s) {
         return cudaGetLastError();
     }
     if (nblocks <= 0) return cudaSuccess;
+    if constexpr (WB_UPDATE_PAIRS && sizeof(T) == 4) {
+        if (a.links) update_kernel2<T, true><<<nblocks, kCellBlock / 2, 0, s>>>(a);
+        else update_kernel2<T, false><<<nblocks, kCellBlock / 2, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.links) update_kernel<T, true><<<nblocks, kCellBlock, 0, s>>>(a);
     else update_kernel<T, false><<<nblocks, kCellBlock, 0, s>>>(a);
     return cudaGetLastError();
