@@ -45,7 +45,7 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # turbulence128.md), scaled by the interface count; valid only while the
 # sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_128 = {"sweep_x": 114.68e6, "sweep_y": 96.65e6, "sweep_z": 97.62e6}
-SWEEP_TRAFFIC_SOURCES = "a47d3d58835ca9f0"
+SWEEP_TRAFFIC_SOURCES = "3b647345c2e43cd9"
 
 
 def sweep_sources_hash() -> str:
