@@ -166,21 +166,23 @@ void orc_flux_n(const double U[8], double gamma, double F[8])
     F[7] = (U[7] + pt) * u - bn * (u * bn + v * b1 + w * b2);
 }
 
-/* Fast, Alfven and slow speeds along the normal axis for primitive W. */
+/* Fast, Alfven and slow speeds along the normal axis for primitive W:
+ * cf^2, cs^2 = (a^2 + b^2 +- D)/2 with D^2 = (a^2 + b^2)^2 - 4 a^2 ca^2, the
+ * roots of the magnetosonic quartic (Sec. 2.1 eigen-system).  Evaluated
+ * without cancellation: D^2 = (a^2 - ca^2)^2 + t (2 (a^2 + ca^2) + t) with
+ * t = B_perp^2/rho (a sum of non-negative terms), cf^2 from the sum, and
+ * cs^2 = a^2 ca^2 / cf^2 (the product of the roots), so that near the
+ * triple point (B_perp -> 0, a^2 -> ca^2) the speeds keep full precision. */
 void orc_wave_speeds(const double W[8], double gamma,
                      double *cf, double *ca, double *cs)
 {
     double rho = W[0];
     double a2 = gamma * W[7] / rho;
     double ca2 = W[4] * W[4] / rho;
-    double b2 = (W[4] * W[4] + W[5] * W[5] + W[6] * W[6]) / rho;
-    double s = a2 + b2;
-    double disc = s * s - 4.0 * a2 * ca2;
-    if (disc < 0.0) disc = 0.0;
-    double q = sqrt(disc);
-    double cf2 = 0.5 * (s + q);
-    double cs2 = 0.5 * (s - q);
-    if (cs2 < 0.0) cs2 = 0.0;
+    double t = (W[5] * W[5] + W[6] * W[6]) / rho;
+    double D = sqrt((a2 - ca2) * (a2 - ca2) + t * (2.0 * (a2 + ca2) + t));
+    double cf2 = 0.5 * ((a2 + ca2 + t) + D);
+    double cs2 = cf2 > 0.0 ? a2 * ca2 / cf2 : 0.0;
     *cf = sqrt(cf2);
     *ca = sqrt(ca2);
     *cs = sqrt(cs2);
@@ -237,8 +239,17 @@ static int invert(int n, const double *A, double *Ainv)
  * Degeneracy rules (identical on every implementation):
  *   beta = B_perp/|B_perp| if |B_perp|^2 > 1e-24 max(1,|B|^2), else 1/sqrt(2);
  *   if cf^2 - cs^2 <= 1e-12 (a^2 + b^2): (alpha_f, alpha_s) = (1,0) when
- *   a^2 >= ca^2, else (0,1); otherwise the usual square roots, clipped at 0;
+ *   a^2 >= ca^2, else (0,1); otherwise alpha_f^2 = (a^2 - cs^2)/(cf^2 - cs^2)
+ *   and alpha_s^2 = (cf^2 - a^2)/(cf^2 - cs^2), evaluated without
+ *   cancellation (below);
  *   sign(B_n) = +1 when B_n = 0.
+ * With t = B_perp^2/rho, D = cf^2 - cs^2 = sqrt((a^2 - ca^2)^2 +
+ * t (2 (a^2 + ca^2) + t)), x = a^2 - cs^2 = (D + a^2 - ca^2 - t)/2 and
+ * y = cf^2 - a^2 = (D - a^2 + ca^2 + t)/2, where x + y = D and x y = a^2 t:
+ * the larger of x, y is taken from its sum (relative error a few units of
+ * rounding, as it is at least D/2) and the smaller from the product, so
+ * that as B_perp -> 0 the vanishing weight goes to zero with B_perp instead
+ * of being the square root of a rounding error.
  * RU and LU are row-major 7x7; column s of RU is the right eigenvector of
  * wave s, row s of LU the left one.  Returns -1 if RU is singular. */
 int orc_eigen(const double W[8], double gamma, double lam[7],
@@ -250,7 +261,7 @@ int orc_eigen(const double W[8], double gamma, double lam[7],
     double a = sqrt(a2);
     double cf, ca, cs;
     orc_wave_speeds(W, gamma, &cf, &ca, &cs);
-    double cf2 = cf * cf, cs2 = cs * cs, ca2 = bn * bn / rho;
+    double ca2 = bn * bn / rho;
     double bperp2 = b1 * b1 + b2 * b2;
     double btot2 = bn * bn + bperp2;
     double beta1, beta2;
@@ -264,14 +275,19 @@ int orc_eigen(const double W[8], double gamma, double lam[7],
     }
     double alf, als;
     double bb2 = btot2 / rho;
-    if (cf2 - cs2 <= 1e-12 * (a2 + bb2)) {
+    double t = bperp2 / rho;
+    double dd = (a2 - ca2) * (a2 - ca2) + t * (2.0 * (a2 + ca2) + t);
+    double D = sqrt(dd);
+    if (D <= 1e-12 * (a2 + bb2)) {
         if (a2 >= ca2) { alf = 1.0; als = 0.0; }
         else           { alf = 0.0; als = 1.0; }
     } else {
-        double t1 = (a2 - cs2) / (cf2 - cs2);
-        double t2 = (cf2 - a2) / (cf2 - cs2);
-        alf = sqrt(t1 > 0.0 ? t1 : 0.0);
-        als = sqrt(t2 > 0.0 ? t2 : 0.0);
+        double x = 0.5 * (D + (a2 - ca2) - t);
+        double y = 0.5 * (D - (a2 - ca2) + t);
+        if (x >= y) y = a2 * t / x;
+        else        x = a2 * t / y;
+        alf = sqrt(x > 0.0 ? x / D : 0.0);
+        als = sqrt(y > 0.0 ? y / D : 0.0);
     }
     double sgn = (bn >= 0.0) ? 1.0 : -1.0;
     double sr = sqrt(rho);

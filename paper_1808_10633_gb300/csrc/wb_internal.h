@@ -111,16 +111,18 @@ __device__ __forceinline__ T cell_signal(T rho, T m0, T m1, T m2, T E, T B0, T B
     const T kin = rn::mul(rn::mul(T(0.5), rho), vv);
     p = rn::mul(rn::sub(g, T(1)), rn::sub(rn::sub(E, kin), rn::mul(T(0.5), bb)));
     const T a2 = rn::mul(rn::mul(g, p), rinv);
-    const T sum = rn::add(a2, rn::mul(bb, rinv));
-    const T s2 = rn::mul(sum, sum), a4 = rn::mul(T(4), a2);
-    const T Bd[3] = {B0, B1, B2}, vd[3] = {v0, v1, v2}, id[3] = {id0, id1, id2};
+    const T q[3] = {rn::mul(B0, B0), rn::mul(B1, B1), rn::mul(B2, B2)};
+    const T vd[3] = {v0, v1, v2}, id[3] = {id0, id1, id2};
     T sp = T(0);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        const T ca2 = rn::mul(rn::mul(Bd[d], Bd[d]), rinv);
-        T disc = rn::sub(s2, rn::mul(a4, ca2));
-        disc = disc > T(0) ? disc : T(0);
-        const T cf = rn::sqrt(rn::mul(T(0.5), rn::add(sum, rn::sqrt(disc))));
+        // cf^2 = (a^2 + ca^2 + t + D)/2, D^2 = (a^2 - ca^2)^2 + t (2 (a^2 + ca^2) + t),
+        // t = B_perp^2 / rho: non-negative terms only (no cancellation)
+        const T ca2 = rn::mul(q[d], rinv);
+        const T t = rn::mul(rn::add(q[(d + 1) % 3], q[(d + 2) % 3]), rinv);
+        const T dA = rn::sub(a2, ca2), sA = rn::add(a2, ca2);
+        const T D = rn::sqrt(rn::add(rn::mul(dA, dA), rn::mul(t, rn::add(rn::mul(T(2), sA), t))));
+        const T cf = rn::sqrt(rn::mul(T(0.5), rn::add(rn::add(sA, t), D)));
         const T av = vd[d] < T(0) ? -vd[d] : vd[d];
         sp = rn::add(sp, rn::mul(rn::add(av, cf), id[d]));
     }

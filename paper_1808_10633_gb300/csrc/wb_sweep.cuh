@@ -258,20 +258,25 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
     double a2 = gamma * p / rho;
     double ca2 = bn * bn / rho;
     double b2r = bt2 / rho;
-    double s = a2 + b2r;
-    double disc = s * s - 4.0 * a2 * ca2;
-    disc = disc > 0.0 ? disc : 0.0;
-    double q = sqrt(disc);
-    double cf2 = 0.5 * (s + q);
-    double cs2 = 0.5 * (s - q);
-    cs2 = cs2 > 0.0 ? cs2 : 0.0;
-    if (cf2 - cs2 <= 1e-12 * (a2 + b2r)) {
+    // D = cf^2 - cs^2 from a sum of non-negative terms (t = B_perp^2 / rho),
+    // cf^2 from the sum of the roots, cs^2 from their product a^2 ca^2: no
+    // cancellation near B_perp -> 0 or the triple point.  alpha_f^2 = x / D,
+    // alpha_s^2 = y / D with x = a^2 - cs^2, y = cf^2 - a^2: the larger of
+    // x, y from x + y = D and the smaller from x y = a^2 t, so the vanishing
+    // weight goes to zero with B_perp
+    const double t = bp2 / rho;
+    const double D = sqrt((a2 - ca2) * (a2 - ca2) + t * (2.0 * (a2 + ca2) + t));
+    const double cf2 = 0.5 * ((a2 + ca2 + t) + D);
+    const double cs2 = cf2 > 0.0 ? a2 * ca2 / cf2 : 0.0;
+    if (D <= 1e-12 * (a2 + b2r)) {
         if (a2 >= ca2) { alf = 1.0; als = 0.0; } else { alf = 0.0; als = 1.0; }
     } else {
-        double r = 1.0 / (cf2 - cs2);
-        double t1 = (a2 - cs2) * r, t2 = (cf2 - a2) * r;
-        alf = sqrt(t1 > 0.0 ? t1 : 0.0);
-        als = sqrt(t2 > 0.0 ? t2 : 0.0);
+        double x = 0.5 * (D + (a2 - ca2) - t);
+        double y = 0.5 * (D - (a2 - ca2) + t);
+        if (x >= y) y = a2 * t / x;
+        else x = a2 * t / y;
+        alf = sqrt(x > 0.0 ? x / D : 0.0);
+        als = sqrt(y > 0.0 ? y / D : 0.0);
     }
     cf2o = cf2;
     cs2o = cs2;
@@ -295,14 +300,12 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
         const T bp2 = b1 * b1 + b2 * b2;
         const T bt2 = bn * bn + bp2;
         const T b2r = bt2 * rinv;
-        const T s = a2 + b2r;
-        T disc = s * s - T(4) * a2 * ca2;
-        disc = tmax(disc, T(0));
-        const T q = sq_root(disc);
-        cf2 = T(0.5) * (s + q);
-        cs2 = tmax(T(0.5) * (s - q), T(0));
+        const T t = bp2 * rinv;
+        const T D = sq_root((a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t));
+        cf2 = T(0.5) * ((a2 + ca2 + t) + D);
+        cs2 = cf2 > T(0) ? a2 * ca2 / cf2 : T(0);
         const bool near_bperp = !(bp2 > T(1e-6) * bt2);
-        const bool near_triple = !(cf2 - cs2 > T(1e-3) * (a2 + b2r));
+        const bool near_triple = !(D > T(1e-3) * (a2 + b2r));
         if (near_bperp || near_triple) {
             double dbe1, dbe2, dalf, dals, dcf2, dcs2;
             degenerate_rules(rho, bn, b1, b2, p, gamma, dbe1, dbe2, dalf, dals, dcf2, dcs2);
@@ -312,9 +315,12 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
             const T bp = sq_root(bp2);
             be1 = b1 / bp;
             be2 = b2 / bp;
-            const T r = T(1) / (cf2 - cs2);
-            alf = sq_root(tmax((a2 - cs2) * r, T(0)));
-            als = sq_root(tmax((cf2 - a2) * r, T(0)));
+            T x = T(0.5) * (D + (a2 - ca2) - t), y = T(0.5) * (D - (a2 - ca2) + t);
+            if (x >= y) y = a2 * t / x;
+            else x = a2 * t / y;
+            const T r = T(1) / D;
+            alf = sq_root(tmax(x * r, T(0)));
+            als = sq_root(tmax(y * r, T(0)));
         }
     }
     const T cf = sq_root(cf2), cs = sq_root(cs2), ca = sq_root(ca2);
@@ -441,12 +447,14 @@ __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell
     sm[(SF + 6) * nc + idx] = (E + pt) * u - bn * vb;
     const T a2 = g * p * rinv;
     const T ca2 = bn * bn * rinv;
-    const T s = a2 + bb * rinv;
-    T disc = s * s - T(4) * a2 * ca2;
-    disc = tmax(disc, T(0));
-    const T qd = sq_root(disc);
-    const T cf = sq_root(T(0.5) * (s + qd));
-    const T cs = sq_root(tmax(T(0.5) * (s - qd), T(0)));
+    // fast and slow speeds without cancellation: D = cf^2 - cs^2 from a sum
+    // of non-negative terms (t = B_perp^2 / rho), cf^2 from the sum of the
+    // roots and cs^2 = a^2 ca^2 / cf^2 from their product
+    const T t = (b1 * b1 + b2 * b2) * rinv;
+    const T D = sq_root((a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t));
+    const T cf2 = T(0.5) * ((a2 + ca2 + t) + D);
+    const T cf = sq_root(cf2);
+    const T cs = sq_root(cf2 > T(0) ? a2 * ca2 / cf2 : T(0));
     const T ca = sq_root(ca2);
     sm[(SL + 0) * nc + idx] = tabs(u - cf);
     sm[(SL + 1) * nc + idx] = tabs(u - ca);

@@ -131,3 +131,24 @@ def test_normalisation_continuous_through_triple_point(orc):
         R = _prim_R(orc, W)
         assert np.isfinite(R).all()
         assert np.linalg.cond(R) < 1e4
+
+
+def test_vanishing_weight_is_exactly_zero_at_bperp_zero(orc):
+    """With B_perp = 0 and a^2 > ca^2 the slow weight alpha_s is exactly 0 in
+    exact arithmetic; the normalisation is evaluated so that it is exactly 0
+    in floating point too (not the square root of a rounding error), so the
+    fast waves carry no transverse field.  With B_perp = d small, alpha_s
+    grows in proportion to d (alpha_s^2 = a^2 t / ((a^2 - cs^2) D))."""
+    W = np.array(STATES["bperp_zero"])               # a^2 = 1.0 > ca^2 = 0.81
+    lam, R, L, st = orc.eigen(W, G)
+    for f in (0, 6):                                  # fast columns; rows B_t1, B_t2
+        assert R[4, f] == 0.0 and R[5, f] == 0.0
+    prev = None
+    for d in [1e-4, 1e-6, 1e-8]:
+        Wd = W.copy()
+        Wd[5] = d
+        _, Rd, _, _ = orc.eigen(Wd, G)
+        bt = abs(Rd[4, 0])                            # alpha_s a sqrt(rho) beta_1, beta_1 = 1
+        if prev is not None:
+            assert bt / prev == pytest.approx(0.01, rel=1e-6)
+        prev = bt
