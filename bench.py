@@ -44,8 +44,8 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # ncu capture of the 128^3 turbulence case (profiles/sweep_kernel_fixed_fp32_
 # turbulence128.md), scaled by the interface count; valid only while the
 # sweep sources hash to SWEEP_TRAFFIC_SOURCES.
-SWEEP_TRAFFIC_128 = {"sweep_x": 114.68e6, "sweep_y": 96.65e6, "sweep_z": 97.62e6}
-SWEEP_TRAFFIC_SOURCES = "3b647345c2e43cd9"
+SWEEP_TRAFFIC_128 = {"sweep_x": 114.09e6, "sweep_y": 96.57e6, "sweep_z": 97.64e6}
+SWEEP_TRAFFIC_SOURCES = "e34db60fac53b289"
 
 
 def sweep_sources_hash() -> str:
