@@ -17,12 +17,14 @@
 // theorem on each face (four edge EMFs per face), so the face divergence of b
 // is unchanged to round-off.
 //
-// Two forms of each kernel share the per-value arithmetic below (written with
-// explicit roundings, so both give identical bits): one thread per cell
-// (any patch, linked patches), and, for periodic patches whose x extent is a
-// multiple of the vector width, one thread per 16-byte vector of cells along
-// x (4 in FP32, 2 in FP64), which keeps four times the bytes in flight per
-// thread on these bandwidth-bound kernels.
+// Three forms of each kernel share the per-value arithmetic below (written
+// with explicit roundings, so all give identical bits): for periodic patches
+// whose x extent is a multiple of the vector width, one thread per 16-byte
+// vector of cells along x (4 in FP32, 2 in FP64), which keeps four times the
+// bytes in flight per thread on these bandwidth-bound kernels; otherwise (any
+// patch, linked patches) two cells per thread with the loads of both issued
+// before the first store (FP32), or one cell per thread (FP64, whose doubled
+// registers would spill).
 #include "wb_internal.h"
 
 // FP32 grids whose per-cell kernels cannot use the vector forms run the
