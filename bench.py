@@ -45,7 +45,7 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # turbulence128.md), scaled by the interface count; valid only while the
 # sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_128 = {"sweep_x": 114.09e6, "sweep_y": 96.57e6, "sweep_z": 97.64e6}
-SWEEP_TRAFFIC_SOURCES = "e34db60fac53b289"
+SWEEP_TRAFFIC_SOURCES = "fd6f568fa6a1c760"
 
 
 def sweep_sources_hash() -> str:

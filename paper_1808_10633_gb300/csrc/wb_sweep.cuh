@@ -792,8 +792,11 @@ template <> struct MinBlocks<float> { static constexpr int value = WB_SWEEP_MINB
 // TP = kSweepNT / TA pencils.  Shape 0 is the default; the host picks a shape per
 // patch (fewest thread slots for the patch's sizes) and stores it in the top
 // byte of the tile's patch field.
+#ifndef WB_SWEEP_TA_X1
+#define WB_SWEEP_TA_X1 8
+#endif
 __host__ __device__ constexpr int shape_ta(int axis, int s) {
-    return axis == 0 ? (s == 0 ? WB_SWEEP_TA_X : (s == 1 ? 64 : 16))
+    return axis == 0 ? (s == 0 ? WB_SWEEP_TA_X : (s == 1 ? WB_SWEEP_TA_X1 : 16))
                      : (s == 0 ? WB_SWEEP_TA_YZ : (s == 1 ? 8 : 32));
 }
 constexpr int kNShape = 3;
