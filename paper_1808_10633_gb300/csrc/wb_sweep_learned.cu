@@ -74,6 +74,9 @@ __device__ __forceinline__ uint32_t gelu2x(float a, float b) {
 
 // One warp, one field: omega (w0, w2) for the 64 rows of `in` (row r holds 8
 // bf16: x0..x5, 1, 0) into om[2r], om[2r+1].
+#ifndef WB_LEARNED_PACKED
+#define WB_LEARNED_PACKED 1            // input normalisation and weights in packed FP32 pairs
+#endif
 #ifndef WB_LEARNED_HOIST
 #define WB_LEARNED_HOIST 1
 #endif
@@ -172,6 +175,9 @@ struct LearnedWeights {
     int nfire = 0;            // detector firings of this thread (fields x sides)
 
     __device__ __forceinline__ float corr(int s, const float (&w)[6], const float (&g)[6], float alpha) {
+#if WB_LEARNED_PACKED
+        return corr_packed(s, w, g, alpha);
+#endif
         const float ha = 0.5f * alpha;
         float vp[6], vm[6];
 #pragma unroll
@@ -222,6 +228,74 @@ struct LearnedWeights {
                                   : w0m * (Dm[0] - 2.f * Dm[1] + Dm[2]) * (1.f / 3.f)
                                         + (w2m - 0.5f) * (Dm[1] - 2.f * Dm[2] + Dm[3]) * (1.f / 6.f);
         return phm - php;
+    }
+
+    // The same in packed FP32 pairs, lane x the '+' side and lane y the '-'
+    // side (its stencil reversed).  The pair differences V_{k+1} - V_k are
+    // (D+_k, -D-_k); both the interpolant and the learned form are odd in D,
+    // so the '-' side's value is the negative of the one taken on -D-.
+    __device__ __forceinline__ float corr_packed(int s, const float (&w)[6], const float (&g)[6], float alpha) {
+        const float2 ha = make_float2(0.5f * alpha, -0.5f * alpha);
+        float2 V[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            V[k] = __ffma2_rn(ha, make_float2(w[k], w[5 - k]), __fmul2_rn(splat2(0.5f), make_float2(g[k], g[5 - k])));
+        float2 D[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) D[k] = __ffma2_rn(V[k], splat2(-1.0f), V[k + 1]);
+        float2 mean = V[0];
+#pragma unroll
+        for (int k = 1; k < 6; k++) mean = __fadd2_rn(mean, V[k]);
+        mean = __fmul2_rn(mean, splat2(1.0f / 6.0f));
+        float2 dv[6];
+        float mxp = 0.f, mxm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            dv[k] = __ffma2_rn(mean, splat2(-1.0f), V[k]);
+            mxp = fmaxf(mxp, fabsf(dv[k].x));
+            mxm = fmaxf(mxm, fabsf(dv[k].y));
+        }
+        const float2 inv = make_float2(__fdividef(1.0f, mxp + 1e-12f), __fdividef(1.0f, mxm + 1e-12f));
+        float2 x[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) x[k] = __fmul2_rn(dv[k], inv);
+        // one 16-byte store per row (rows 2 lane, 2 lane + 1: the two sides)
+        *reinterpret_cast<uint4*>(in + (2 * lane) * 4) =
+            make_uint4(pack_bf16(x[0].x, x[1].x), pack_bf16(x[2].x, x[3].x), pack_bf16(x[4].x, x[5].x),
+                       pack_bf16(1.0f, 0.0f));
+        *reinterpret_cast<uint4*>(in + (2 * lane + 1) * 4) =
+            make_uint4(pack_bf16(x[0].y, x[1].y), pack_bf16(x[2].y, x[3].y), pack_bf16(x[4].y, x[5].y),
+                       pack_bf16(1.0f, 0.0f));
+        bool fire[2];
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            float dmax = 0.f, dsum = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float a = fabsf(side == 0 ? D[k].x : D[k].y);
+                dmax = fmaxf(dmax, a);
+                dsum += a;
+            }
+            fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f;
+            nfire += fire[side] ? 1 : 0;
+        }
+        __syncwarp();
+        mlp_warp(W + s * kMlpWords * 32, in, om, lane);
+        __syncwarp();
+        const float4 wl = *reinterpret_cast<const float4*>(om + 4 * lane);
+        __syncwarp();
+        const float2 w0 = make_float2(wl.x, wl.z), w2 = make_float2(wl.y, wl.w);
+        const float2 pp = __ffma2_rn(D[1], splat2(-2.0f), __fadd2_rn(D[0], D[2]));
+        const float2 qq = __ffma2_rn(D[2], splat2(-2.0f), __fadd2_rn(D[1], D[3]));
+        float2 ph = __ffma2_rn(__fmul2_rn(w0, splat2(1.0f / 3.0f)), pp,
+                               __fmul2_rn(__fmul2_rn(__fadd2_rn(w2, splat2(-0.5f)), splat2(1.0f / 6.0f)), qq));
+        if (fire[0] || fire[1]) {
+            const float2 js = phi_n2(D[0], D[1], D[2], D[3]);
+            if (fire[0]) ph.x = js.x;
+            if (fire[1]) ph.y = js.y;
+        }
+        // phm - php with phm = -(value on -D-)
+        return -ph.y - ph.x;
     }
 };
 
