@@ -84,3 +84,20 @@ def test_null_arguments_are_rejected(lib):
     assert lib.wb_cfl_dt(None, 0.4, ctypes.byref(out)) == wombat.WB_EINVAL
     assert lib.wb_conserved_totals(None, None) == wombat.WB_EINVAL
     assert lib.wb_destroy(None) == wombat.WB_OK
+
+
+@pytest.mark.parametrize("dims", [(0, 8, 8), (8, -1, 8), (8, 8, 0), (4097, 8, 8), (2048, 2048, 1024)])
+def test_empty_or_oversized_patches_are_rejected_on_the_host(lib, dims):
+    """A patch with an empty axis, an axis beyond 4096 cells or 2^31 cells or
+    more is refused before any device work (WB_EINVAL, message set)."""
+    from paper_1808_10633_gb300 import wombat
+
+    d, _ = _desc(wombat)
+    arr = np.array(dims, dtype=np.int32)
+    d.dims = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    U = np.zeros(8)
+    b = np.zeros(3)
+    h = ctypes.c_void_p()
+    rc = lib.wb_init_grid(ctypes.byref(d), U.ctypes.data, b.ctypes.data, None, ctypes.byref(h))
+    assert rc == wombat.WB_EINVAL
+    assert b"patch 0" in lib.wb_last_error()
