@@ -9,7 +9,9 @@ Network (one per characteristic field s = 0..6, 1 379 parameters each):
     h2 = gelu(W2 h1 + b2)     W2: 32x32, b2: 32
     z  = W3 h2 + b3           W3: 3x32,  b3: 3
     omega = softmax(z)
-gelu(t) = t/2 (1 + tanh(sqrt(2/pi) (t + 0.044715 t^3))).
+gelu(t) = t sigma(1.702 t) = t/2 (1 + tanh(0.851 t)), the sigmoid form of the
+GELU (its inner argument is linear in t, so on the GPU it folds into the
+layer's weights).
 Flat parameter order per field: W1 (row-major), b1, W2, b2, W3, b3.
 
 Input of one side of one interface: the six split characteristic fluxes of
@@ -30,7 +32,7 @@ D_LIN = np.array([0.1, 0.6, 0.3])
 NIN, NH, NOUT = 6, 32, 3
 NPARAM = NH * NIN + NH + NH * NH + NH + NOUT * NH + NOUT      # 1379
 NFIELD = 7
-C_GELU = np.sqrt(2.0 / np.pi)
+K_GELU = 1.702          # gelu(t) = t sigma(K t)
 
 
 def unpack(p):
@@ -51,13 +53,12 @@ def pack(W1, b1, W2, b2, W3, b3):
 
 
 def gelu(t):
-    return 0.5 * t * (1.0 + np.tanh(C_GELU * (t + 0.044715 * t ** 3)))
+    return 0.5 * t * (1.0 + np.tanh(0.5 * K_GELU * t))
 
 
 def gelu_grad(t):
-    u = C_GELU * (t + 0.044715 * t ** 3)
-    th = np.tanh(u)
-    return 0.5 * (1.0 + th) + 0.5 * t * (1.0 - th * th) * C_GELU * (1.0 + 3 * 0.044715 * t * t)
+    sig = 0.5 * (1.0 + np.tanh(0.5 * K_GELU * t))         # sigma(K t)
+    return sig + K_GELU * t * sig * (1.0 - sig)
 
 
 def softmax(z):

@@ -39,12 +39,12 @@ static_assert(O_B3 + NOUT == NP, "parameter layout");
 constexpr int S_X = 0, S_H1 = 6, S_H2 = 38, S_DA1 = 70, S_DA2 = 102, S_DZ = 134, S_L = 137,
               SREC = 138;
 
+// GELU in its sigmoid form, gelu(t) = t sigma(1.702 t) = t/2 (1 + tanh(0.851 t)),
+// and its derivative sigma + 1.702 t sigma (1 - sigma).
 __device__ __forceinline__ float gelu(float t, float& dgelu) {
-    const float c = 0.7978845608028654f;     // sqrt(2/pi)
-    const float u = c * (t + 0.044715f * t * t * t);
-    const float th = tanhf(u);
-    dgelu = 0.5f * (1.0f + th) + 0.5f * t * (1.0f - th * th) * c * (1.0f + 3.0f * 0.044715f * t * t);
-    return 0.5f * t * (1.0f + th);
+    const float sig = 0.5f * (1.0f + tanhf(0.851f * t));
+    dgelu = sig + 1.702f * t * sig * (1.0f - sig);
+    return t * sig;
 }
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {

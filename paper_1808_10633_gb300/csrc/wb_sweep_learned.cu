@@ -14,9 +14,9 @@
 // layers), BF16 operands and FP32 accumulators.  A layer's accumulator
 // fragments are re-packed in registers as the next layer's A fragments; the
 // weights sit in shared memory already in B-fragment order (34 words per lane
-// per field, written by wb_set_mlp on the host side).  GELU uses the
-// hardware tanh approximation on BF16 pairs and returns twice its value;
-// the hidden and output weights are stored halved to match.  Batch rows are
+// per field, written by wb_set_mlp on the host side).  The GELU (sigmoid
+// form) takes one hardware tanh and one FMA on BF16 pairs, the constant of
+// its argument folded into the stored weights (gelu_k).  Batch rows are
 // independent, so a lane whose interface lies outside the patch still joins
 // the warp-wide products (with a valid stencil) and only skips its store.
 #include "wb_sweep.cuh"
@@ -31,6 +31,7 @@ namespace {
 #endif
 
 constexpr int kMlpWords = 34;                    // per lane per field
+constexpr float kGeluK = 0.851f;                 // gelu(x) = x/2 (1 + tanh(kGeluK x))
 constexpr int kMlpSmemWords = WB_MLP_NFIELD * kMlpWords * 32;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -54,21 +55,18 @@ __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], u
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Twice the GELU of two FP32 accumulators, returned as the next layer's BF16
-// operand pair: with u = c x (1 + 0.044715 x^2), t = tanh(u), the pair
-// x + x t = 2 gelu(x), on the packed pair in BF16 (its result is rounded to
-// BF16 anyway).  The factor 2 is taken out of the next layer's weights, which
-// the host stores halved (exact in BF16), so the layer sees W gelu(x).
-__device__ __forceinline__ uint32_t gelu2x(float a, float b) {
-    const uint32_t x = pack_bf16(a, b);
-    const uint32_t k0 = pack_bf16(0.7978845608f, 0.7978845608f);                 // sqrt(2/pi)
-    const uint32_t k1 = pack_bf16(0.7978845608f * 0.044715f, 0.7978845608f * 0.044715f);
-    uint32_t x2, p, u, t, r;
-    asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(x2) : "r"(x));
-    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(x2), "r"(k1), "r"(k0));    // c (1 + 0.044715 x^2)
-    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(x), "r"(p));
-    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(u));
-    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(x), "r"(t));                // x + x t
+// The GELU in its sigmoid form, gelu(x) = x sigma(1.702 x) = x/2 (1 +
+// tanh(0.851 x)), on two FP32 accumulators, returned as the next layer's BF16
+// operand pair.  The host stores every layer's pre-activation scaled by
+// k = 0.851 (the first layer's weights and bias and the hidden bias times k,
+// the hidden weights halved), so the accumulators hold y = k x and the pair
+// y + y tanh(y) = 2 k gelu(x) needs one tanh and one fused multiply-add on
+// the packed BF16 pair; the output layer's weights are divided by 2 k.
+__device__ __forceinline__ uint32_t gelu_k(float a, float b) {
+    const uint32_t y = pack_bf16(a, b);
+    uint32_t t, r;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(y));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(y), "r"(t));                // y + y t
     return r;
 }
 
@@ -118,10 +116,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
         uint32_t A2[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A2[kt][0] = gelu2x(c1[2 * kt][0], c1[2 * kt][1]);
-            A2[kt][1] = gelu2x(c1[2 * kt][2], c1[2 * kt][3]);
-            A2[kt][2] = gelu2x(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
-            A2[kt][3] = gelu2x(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
+            A2[kt][0] = gelu_k(c1[2 * kt][0], c1[2 * kt][1]);
+            A2[kt][1] = gelu_k(c1[2 * kt][2], c1[2 * kt][3]);
+            A2[kt][2] = gelu_k(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
+            A2[kt][3] = gelu_k(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
         }
         float c2[4][4];
 #pragma unroll
@@ -135,10 +133,10 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
         uint32_t A3[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A3[kt][0] = gelu2x(c2[2 * kt][0], c2[2 * kt][1]);
-            A3[kt][1] = gelu2x(c2[2 * kt][2], c2[2 * kt][3]);
-            A3[kt][2] = gelu2x(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
-            A3[kt][3] = gelu2x(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
+            A3[kt][0] = gelu_k(c2[2 * kt][0], c2[2 * kt][1]);
+            A3[kt][1] = gelu_k(c2[2 * kt][2], c2[2 * kt][3]);
+            A3[kt][2] = gelu_k(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
+            A3[kt][3] = gelu_k(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
         }
         const float b3lo = Wf(32), b3hi = Wf(33);
         float c3[4] = {b3lo, b3hi, b3lo, b3hi};
@@ -466,8 +464,13 @@ void mlp_fragments(const float* params, uint32_t* out) {
         const float* W3 = b2 + NH;
         const float* b3 = W3 + 3 * NH;
         // first layer as 32 x 8: six weights, the bias, a zero
-        auto w1 = [&](int n, int k) { return k < NIN ? W1[n * NIN + k] : (k == NIN ? b1[n] : 0.f); };
-        auto w3 = [&](int n, int k) { return n < 3 ? 0.5f * W3[n * NH + k] : 0.f; };
+        // pre-activations scaled by kGeluK (see gelu_k): first layer (with its
+        // bias) and hidden bias times kGeluK, hidden weights halved, output
+        // weights divided by 2 kGeluK
+        auto w1 = [&](int n, int k) {
+            return kGeluK * (k < NIN ? W1[n * NIN + k] : (k == NIN ? b1[n] : 0.f));
+        };
+        auto w3 = [&](int n, int k) { return n < 3 ? W3[n * NH + k] / (2.0f * kGeluK) : 0.f; };
         for (int lane = 0; lane < 32; lane++) {
             const int g = lane >> 2, t = lane & 3;
             uint32_t* o = out + (size_t)f * kMlpWords * 32 + lane;
@@ -475,7 +478,8 @@ void mlp_fragments(const float* params, uint32_t* out) {
             for (int nt = 0; nt < 4; nt++)
                 for (int kt = 0; kt < 2; kt++) {
                     const int n = 8 * nt + g, k0 = 16 * kt + 2 * t;
-                    // hidden and output weights halved: the kernel's GELU returns 2 gelu
+                    // hidden weights halved: the layer's input is 2 kGeluK gelu, its
+                    // output is wanted times kGeluK
                     o[(4 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0], 0.5f * W2[n * NH + k0 + 1]);
                     o[(5 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0 + 8], 0.5f * W2[n * NH + k0 + 9]);
                 }
@@ -485,8 +489,8 @@ void mlp_fragments(const float* params, uint32_t* out) {
                 o[(21 + kt * 2) * 32] = pk(w3(g, k0 + 8), w3(g, k0 + 9));
             }
             for (int nt = 0; nt < 4; nt++) {
-                o[(24 + 2 * nt) * 32] = fbits(b2[8 * nt + 2 * t]);
-                o[(25 + 2 * nt) * 32] = fbits(b2[8 * nt + 2 * t + 1]);
+                o[(24 + 2 * nt) * 32] = fbits(kGeluK * b2[8 * nt + 2 * t]);
+                o[(25 + 2 * nt) * 32] = fbits(kGeluK * b2[8 * nt + 2 * t + 1]);
             }
             o[32 * 32] = fbits(2 * t < 3 ? b3[2 * t] : 0.f);
             o[33 * 32] = fbits(2 * t + 1 < 3 ? b3[2 * t + 1] : 0.f);

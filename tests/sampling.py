@@ -33,18 +33,26 @@ def bf16(a):
 
 
 def learned_params_as_run(params):
-    """The network parameters as the tensor-core sweep uses them: weights
-    (and the first layer's bias, fed as a weight) rounded to BF16, the hidden
-    and output biases kept FP32."""
+    """The network parameters as the tensor-core sweep uses them: it stores
+    the first layer (weights and bias, the bias fed as a weight) times
+    k = 0.851 in BF16, the hidden weights halved in BF16, the hidden bias
+    times k in FP32, the output weights divided by 2 k in BF16 and the output
+    bias in FP32 (the GELU's argument constant folded into the weights); the
+    values returned are those divided back by the same factors."""
     from oracle import learned as Lr
 
-    p64 = np.asarray(params, np.float64).reshape(7, Lr.NPARAM)
-    P = bf16(params).reshape(7, Lr.NPARAM).copy()
-    o = 32 * 6
-    P[:, o:o + 32] = bf16(p64[:, o:o + 32])
-    o2 = o + 32 + 32 * 32
-    P[:, o2:o2 + 32] = p64[:, o2:o2 + 32]
-    P[:, -3:] = p64[:, -3:]
+    k = np.float32(0.851)
+    p32 = np.asarray(params, np.float32).reshape(7, Lr.NPARAM)
+    P = np.asarray(params, np.float64).reshape(7, Lr.NPARAM).copy()
+    n1 = 32 * 6 + 32                                   # W1 and b1
+    P[:, :n1] = bf16(p32[:, :n1] * k) / np.float64(k)
+    o2 = n1
+    P[:, o2:o2 + 32 * 32] = bf16(p32[:, o2:o2 + 32 * 32] * np.float32(0.5)) * 2.0
+    ob2 = o2 + 32 * 32
+    P[:, ob2:ob2 + 32] = (p32[:, ob2:ob2 + 32] * k).astype(np.float64) / np.float64(k)
+    o3 = ob2 + 32
+    k2 = np.float32(2.0) * k
+    P[:, o3:o3 + 3 * 32] = bf16(p32[:, o3:o3 + 3 * 32] / k2) * np.float64(k2)
     return P
 
 
