@@ -76,7 +76,7 @@ __device__ __forceinline__ uint32_t gelu_k(float a, float b) {
 #define WB_LEARNED_PACKED 1            // input normalisation and weights in packed FP32 pairs
 #endif
 #ifndef WB_LEARNED_HOIST
-#define WB_LEARNED_HOIST 1
+#define WB_LEARNED_HOIST 0
 #endif
 // This lane's fragment words of one field: read from shared memory at each
 // use, or (WB_LEARNED_HOIST) once into registers for all four row tiles.
