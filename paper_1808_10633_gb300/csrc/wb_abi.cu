@@ -1022,13 +1022,17 @@ int candidate_policy(int c) { return c == 0 ? -1 : (c <= wb::kNTileShape ? c - 1
 // Builds and uploads the tile table of `axis` for `policy` (synchronous).
 int install_tiles(wb_grid* g, int axis, int policy) {
     std::vector<wb::Tile> t = build_tiles(g, axis, policy);
-    if ((int)t.size() != g->ntiles[axis]) {
-        cudaFree(g->d_tiles[axis]);
-        g->d_tiles[axis] = nullptr;
-        WB_CK(cudaMalloc(&g->d_tiles[axis], sizeof(wb::Tile) * t.size()));
-        g->ntiles[axis] = (int)t.size();
+    // the new table is uploaded into its own buffer first: on failure the
+    // grid keeps its current table
+    wb::Tile* d = nullptr;
+    WB_CK(cudaMalloc(&d, sizeof(wb::Tile) * t.size()));
+    if (cudaMemcpy(d, t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return fail(WB_ECUDA, "tile table upload failed");
     }
-    WB_CK(cudaMemcpy(g->d_tiles[axis], t.data(), sizeof(wb::Tile) * t.size(), cudaMemcpyHostToDevice));
+    cudaFree(g->d_tiles[axis]);
+    g->d_tiles[axis] = d;
+    g->ntiles[axis] = (int)t.size();
     g->tile_policy[axis] = policy;
     tile_split(t, g->tile_split[axis]);
     if (g->graph) {              // tile tables changed: capture again
