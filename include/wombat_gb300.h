@@ -67,7 +67,7 @@ typedef enum {
 } wb_integrator;
 
 typedef struct {
-    int npatch;           /* number of independent periodic patches (>= 1)   */
+    int npatch;           /* number of patches, 1 <= npatch < 2^24            */
     const int *dims;      /* host, npatch*3 interior sizes (nx, ny, nz), each
                              in [1, 4096]; copied                            */
     double dx, dy, dz;    /* cell sizes (> 0), shared by all patches         */
@@ -114,7 +114,8 @@ typedef struct {
  * divergence is preserved by the constrained transport.  cuda_stream: a
  * cudaStream_t to order all work on, or NULL for a stream the library
  * creates.  out: receives the grid.  Synchronises.
- * Errors: WB_EINVAL for a null pointer, npatch < 1, a size out of range,
+ * Errors: WB_EINVAL for a null pointer, npatch < 1 or >= 2^24, a patch
+ * extent outside [1, 4096] or a patch of 2^31 cells or more,
  * ghost != 3, an unknown mode, WENO-Z with learned weights,
  * non-positive dx/dy/dz or gamma <= 1, or an inconsistent link table;
  * WB_ENOMEM; WB_ECUDA. */

@@ -587,6 +587,8 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
     if (!d || !U0 || !b0 || !out) return fail(WB_EINVAL, "null argument");
     *out = nullptr;
     if (d->npatch < 1 || !d->dims) return fail(WB_EINVAL, "npatch must be >= 1 with dims");
+    // a sweep tile keeps its patch index in 24 bits (the top byte holds the shape)
+    if (d->npatch >= (1 << 24)) return fail(WB_EINVAL, "npatch must be < 2^24, got %d", d->npatch);
     if (d->ghost != 3) return fail(WB_EINVAL, "ghost must be 3 (WENO5 stencil), got %d", d->ghost);
     if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return fail(WB_EINVAL, "dx, dy, dz must be > 0");
     if (!(d->gamma > 1.0)) return fail(WB_EINVAL, "gamma must be > 1");

@@ -58,7 +58,7 @@ def _desc(wombat, **over):
     return wombat.GridDesc(**kw), dims
 
 
-@pytest.mark.parametrize("bad", [dict(ghost=2), dict(npatch=0), dict(dx=0.0), dict(gamma=1.0),
+@pytest.mark.parametrize("bad", [dict(ghost=2), dict(npatch=0), dict(npatch=1 << 24), dict(dx=0.0), dict(gamma=1.0),
                                  dict(precision=7), dict(integrator=5), dict(emf_mode=3),
                                  dict(weights=2), dict(weights=1, precision=2)])
 def test_invalid_descriptor_is_rejected_on_the_host(lib, bad):
