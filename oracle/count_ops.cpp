@@ -30,8 +30,6 @@ struct cdouble {
     double v;
     cdouble() = default;
     constexpr cdouble(double x) : v(x) {}
-    explicit constexpr cdouble(long double x) : v((double)x) {}
-    explicit constexpr operator long double() const { return v; }
     explicit constexpr operator long() const { return (long)v; }
     explicit constexpr operator int() const { return (int)v; }
     cdouble& operator+=(cdouble b);
@@ -75,8 +73,6 @@ inline cdouble fabs(cdouble a) { return cdouble(::fabs(a.v)); }
 
 static_assert(sizeof(cdouble) == sizeof(double), "cdouble must have the layout of double");
 
-typedef long double orc_wide_t;
-#define ORC_WIDE orc_wide_t
 #define double cdouble
 #include "wb_oracle.c"
 #undef double

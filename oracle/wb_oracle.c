@@ -24,12 +24,6 @@
 #endif
 #include "wb_oracle.h"
 
-/* extended-precision accumulator of the totals (a name of its own so that
- * the operation-counting build, count_ops.cpp, can keep it) */
-#ifndef ORC_WIDE
-#define ORC_WIDE long double
-#endif
-
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
@@ -736,15 +730,26 @@ double orc_cfl_dt(const orc_grid *g, double cfl, const double *U)
     return cfl / orc_cfl_speed(g, U);
 }
 
-/* Conserved totals sum_cells U_q dV, accumulated in long double. */
+/* Conserved totals sum_cells U_q dV.  The sum over cells is compensated
+ * (Neumaier 1974): the rounding error of every addition is recovered exactly
+ * from the larger and the smaller operand and kept in a second double, which
+ * is added back once at the end.  The result is within a few units in the
+ * last place of the exact sum, and, being plain IEEE double arithmetic
+ * without contraction, the same bits on every host. */
 void orc_totals(const orc_grid *g, const double *U, double out[8])
 {
     long N = ncell(g);
     double dV = g->dx * g->dy * g->dz;
     for (int q = 0; q < 8; q++) {
-        ORC_WIDE acc = 0.0L;
-        for (long c = 0; c < N; c++) acc += (ORC_WIDE)U[q * N + c];
-        out[q] = (double)(acc * (ORC_WIDE)dV);
+        double s = 0.0, comp = 0.0;
+        for (long c = 0; c < N; c++) {
+            double x = U[q * N + c];
+            double t = s + x;
+            if (fabs(s) >= fabs(x)) comp += (s - t) + x;
+            else                    comp += (x - t) + s;
+            s = t;
+        }
+        out[q] = (s + comp) * dV;
     }
 }
 

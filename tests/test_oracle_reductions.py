@@ -59,3 +59,21 @@ def test_cell_b_is_face_mean(orc):
     assert np.array_equal(U[4], 0.5 * (st.bx + np.roll(st.bx, -1, axis=2)))
     assert np.array_equal(U[5], 0.5 * (st.by + np.roll(st.by, -1, axis=1)))
     assert np.array_equal(U[6], 0.5 * (st.bz + np.roll(st.bz, -1, axis=0)))
+
+
+def test_totals_recover_the_digits_a_plain_sum_loses(orc):
+    """Sum 1e16 + 1 - 1e16 + 1 (and shuffled sign patterns) along the cells:
+    the exact total is 2 (and so on), which a plain left-to-right FP64 sum
+    misses (1e16 + 1 rounds to 1e16).  The compensated sum is exact here, and
+    the same bits on every IEEE host."""
+    g = orc.Grid(4, 1, 1, 1.0, 1.0, 1.0)
+    U = np.zeros((8, 1, 1, 4))
+    U[0] = 1.0
+    bz = np.zeros((1, 1, 4))
+    for vals, exact in (([1e16, 1.0, -1e16, 1.0], 2.0), ([1.0, 1e16, 1.0, -1e16], 2.0),
+                        ([3.0, 2.0 ** 60, -(2.0 ** 60), 0.5], 3.5)):
+        U[0, 0, 0] = vals
+        got = orc.totals(g, U, bz, bz, bz)
+        assert got[0] == exact, (vals, got[0])
+    # a plain sum of the first pattern would give 1
+    assert ((1e16 + 1.0) - 1e16) + 1.0 == 1.0
