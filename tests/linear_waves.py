@@ -52,11 +52,13 @@ def eigen(mode, gamma=GAMMA):
     return lam[k], r
 
 
-def state(N, mode, amp=1e-5, t=0.0, ny=1, gamma=GAMMA):
-    """(U[8, ny, ny, N], bx, by, bz, dx, lam) of the wave at time t."""
+def state(N, mode, amp=1e-5, t=0.0, ny=1, gamma=GAMMA, offset=0.5):
+    """(U[8, ny, ny, N], bx, by, bz, dx, lam) of the wave at time t, sampled
+    at x = (i + offset)/N (offset 0: the points of grid N are every m-th
+    point of grid m N, for self-convergence against a finer run)."""
     lam, r = eigen(mode, gamma)
     X0, bn = background(mode, gamma)
-    x = (np.arange(N) + 0.5) / N
+    x = (np.arange(N) + offset) / N
     X = X0[:, None] + amp * r[:, None] * np.sin(2 * np.pi * (x - lam * t))[None, :]
     shape = (ny, ny, N)
     U = np.empty((8,) + shape)
