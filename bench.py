@@ -40,11 +40,12 @@ UNIT = "zone-updates/s"
 SWEEP_FLOPS_PER_INTERFACE = 2040
 SWEEP_FLOPS_PER_STAGED_CELL = 80
 
-# DRAM bytes (read + write) per launch of the FP32 sweep kernels, from one
-# ncu capture of the 128^3 turbulence case (profiles/sweep_kernel_fixed_fp32_
-# turbulence128.md), scaled by the interface count; valid only while the
-# sweep sources hash to SWEEP_TRAFFIC_SOURCES.
-SWEEP_TRAFFIC_128 = {"sweep_x": 114.09e6, "sweep_y": 96.57e6, "sweep_z": 97.64e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# FP32 sweep kernels, from one ncu capture of the 256^3 turbulence launch this
+# benchmark times (profiles/sweep_traffic_fp32_turbulence256.md); reported
+# only at that size and while the sweep sources hash to SWEEP_TRAFFIC_SOURCES.
+SWEEP_TRAFFIC_N = 256
+SWEEP_TRAFFIC = {"sweep_x": 1188.85e6, "sweep_y": 982.59e6, "sweep_z": 984.48e6}
 SWEEP_TRAFFIC_SOURCES = "fd6f568fa6a1c760"
 
 
@@ -255,15 +256,16 @@ def run_native(args, rank, world, local):
         flops = iface * SWEEP_FLOPS_PER_INTERFACE + staged[cls] * SWEEP_FLOPS_PER_STAGED_CELL
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         traffic = None
-        if label == "float" and sweep_sources_hash() == SWEEP_TRAFFIC_SOURCES:
-            traffic = SWEEP_TRAFFIC_128[cls] * (n / 128) ** 3
+        if label == "float" and n == SWEEP_TRAFFIC_N and sweep_sources_hash() == SWEEP_TRAFFIC_SOURCES:
+            traffic = SWEEP_TRAFFIC[cls]
+        alg_bytes = iface * 4 * (8 + 7 + (3 if cls == "sweep_x" else 0)) * (1 if label == "float" else 2)
         return {"kernel": f"sweep_kernel_fixed<{label},{'xyz'[('sweep_x','sweep_y','sweep_z').index(cls)]}>",
                 "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
                 "traffic_note": None if traffic is None else
-                "ncu dram read+write of the 128^3 case scaled by interfaces (bytes per launch)",
-                "algorithmic_bytes_per_launch": iface * 4 * (8 + 7 + (3 if cls == "sweep_x" else 0))
-                * (1 if label == "float" else 2),
+                f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch at {n}^3 (bytes per launch)",
+                "traffic_vs_algorithmic": None if traffic is None else round(traffic / alg_bytes, 4),
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "flops_per_launch": flops, "ms_per_launch": round(per_launch_ms, 4),
                 "peak_source": "measured FMA throughput (wb_alu_peak) on this GPU"}
 

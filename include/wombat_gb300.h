@@ -344,6 +344,17 @@ int wb_harvest(wb_grid *g, int axis, const long long *cells, long long n,
                const double *hU, const double *hF, double kappa, double pjump,
                float *records_out);
 
+/* The rotated conservative 7-vector X = (rho, m_n, m_t1, m_t2, B_t1, B_t2, E)
+ * of every cell of patch 0 of a periodic FP64 grid, and its physical ideal-
+ * MHD flux F along `axis` (0 x, 1 y, 2 z; n = axis, t1 = axis+1, t2 =
+ * axis+2 mod 3), with the cell field the mean of the cell's two faces
+ * (Sec. 2.1: the flux of the state the sweep projects).  X_out, F_out:
+ * host, 7 * nx*ny*nz doubles each, field-major, x fastest.  The training
+ * pipeline reconstructs the exact face values hU, hF of wb_harvest from
+ * them.  Synchronises.  Errors: WB_EINVAL (not FP64, linked grid, bad axis),
+ * WB_ECUDA. */
+int wb_cell_state_flux(wb_grid *g, int axis, double *X_out, double *F_out);
+
 /* Install the learned-weight networks on a WB_FP32_LEARNED grid (required
  * before its first step).  params: host, WB_MLP_NFIELD * WB_MLP_NPARAM
  * floats (copied, rounded to BF16 for the tensor cores).  kappa: jump

@@ -990,6 +990,29 @@ int wb_harvest(wb_grid* g, int axis, const long long* cells, long long n, const 
     return WB_OK;
 }
 
+int wb_cell_state_flux(wb_grid* g, int axis, double* X_out, double* F_out) {
+    g_err.clear();
+    if (!g || !X_out || !F_out) return fail(WB_EINVAL, "cell_state_flux: null argument");
+    if (g->precision != WB_FP64) return fail(WB_EINVAL, "cell_state_flux: needs an FP64 grid");
+    if (axis < 0 || axis > 2) return fail(WB_EINVAL, "cell_state_flux: axis must be 0, 1 or 2");
+    if (g->d_links) return fail(WB_EINVAL, "cell_state_flux: needs a periodic patch 0 (grid has links)");
+    const wb::PatchDev& P = g->h_patches[0];
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    WB_CK(cudaSetDevice(g->device));
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * 14 * np);
+    if (e == cudaSuccess)
+        e = wb::launch_cell_state_flux<double>(static_cast<const double*>(g->un), g->N, P, axis, g->gamma,
+                                               d, d + 7 * np, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X_out, d, sizeof(double) * 7 * np, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(F_out, d + 7 * np, sizeof(double) * 7 * np, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return fail(WB_ECUDA, "cell_state_flux: %s", cudaGetErrorString(e));
+    return WB_OK;
+}
+
 int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
     g_err.clear();
     if (!g || !params) return fail(WB_EINVAL, "null argument");

@@ -210,6 +210,10 @@ cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, in
                            double gamma, double kappa, double pjump, float* out, cudaStream_t s);
 
 template <class T>
+cudaError_t launch_cell_state_flux(const T* src, long long ncells, const PatchDev& P, int axis,
+                                   double gamma, double* X, double* F, cudaStream_t s);
+
+template <class T>
 cudaError_t launch_cfl(const T* state, const CellBlock* blocks, const PatchDev* patches,
                        const int* links, long long ncells, int nblocks, const CellBlock* vblocks,
                        int nvblocks, double idx, double idy, double idz, double gamma,

@@ -1194,7 +1194,49 @@ __global__ void __launch_bounds__(32) harvest_kernel(const HarvestArgs<T> H) {
     else harvest_one<T, 2>(H, t, sm, nc, base, bp, 32);
 }
 
+// Rotated conserved 7-vector (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and its
+// physical flux along AXIS for every cell of a periodic patch: the sweep's
+// own staging arithmetic (cell B from the faces, rotation, primitives, flux),
+// written as FP64 arrays [7][cells] each.  The training pipeline reconstructs
+// exact face values of these for its targets.
+template <class T, int AXIS>
+__global__ void __launch_bounds__(128) cell_state_flux_kernel(const SweepArgs<T> A, const PatchDev P,
+                                                              double* __restrict__ X,
+                                                              double* __restrict__ F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    const int nc = blockDim.x;
+    const int i = (int)(t % P.nx), j = (int)((t / P.nx) % P.ny), k = (int)(t / ((long long)P.nx * P.ny));
+    RawCell<T> r;
+    long long c;
+    load_cell<T>(A, P, i, j, k, r, c);
+    derive_cell<T, AXIS>(A, r, c, sm, nc, threadIdx.x, false);
+    for (int f = 0; f < 7; f++) {
+        X[f * np + t] = double(sm[(SU + f) * nc + threadIdx.x]);
+        F[f * np + t] = double(sm[(SF + f) * nc + threadIdx.x]);
+    }
+}
+
 }  // namespace
+
+template <class T>
+cudaError_t launch_cell_state_flux(const T* src, long long ncells, const PatchDev& P, int axis,
+                                   double gamma, double* X, double* F, cudaStream_t s) {
+    SweepArgs<T> A;
+    A.src = src; A.flux = nullptr; A.er = nullptr; A.tiles = nullptr; A.patches = nullptr;
+    A.ncells = ncells; A.gamma = gamma;
+    const long long np = (long long)P.nx * P.ny * P.nz;
+    const int nt = 128;
+    const unsigned nb = (unsigned)((np + nt - 1) / nt);
+    const size_t smem = sizeof(T) * kNSlot * nt;
+    if (axis == 0) cell_state_flux_kernel<T, 0><<<nb, nt, smem, s>>>(A, P, X, F);
+    else if (axis == 1) cell_state_flux_kernel<T, 1><<<nb, nt, smem, s>>>(A, P, X, F);
+    else cell_state_flux_kernel<T, 2><<<nb, nt, smem, s>>>(A, P, X, F);
+    return cudaGetLastError();
+}
 
 template <class T>
 cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, int axis,

@@ -15,5 +15,7 @@ template cudaError_t launch_harvest<double>(const double*, long long, const Patc
                                             const long long*, long long, const double*,
                                             const double*, double, double, double, float*,
                                             cudaStream_t);
+template cudaError_t launch_cell_state_flux<double>(const double*, long long, const PatchDev&, int,
+                                                    double, double*, double*, cudaStream_t);
 
 }  // namespace wb

@@ -7,9 +7,11 @@ states, training with the library's CUDA kernels).
    exactly in Fourier space (h^(k) = F^(k) (theta/2)/sin(theta/2), theta =
    2 pi k / N, shifted by half a cell): `face_reconstruction`.  This is exact
    for band-limited data such as the seeded turbulence states.
-2. Records.  `harvest` samples faces of an FP64 grid and lets the library
-   (wb_harvest) project stencils and targets on the interface eigenvectors,
-   split them, normalise them and flag detector hits.
+2. Records.  `harvest` takes each cell's rotated state and physical flux
+   from the library (wb_cell_state_flux), reconstructs their face values,
+   samples faces and lets the library (wb_harvest) project stencils and
+   targets on the interface eigenvectors, split them, normalise them and
+   flag detector hits.
 3. Training.  `train` runs the library's forward/backward/Adam kernels
    (wb_mlp_train) on the unflagged records.
 
@@ -23,24 +25,6 @@ from . import wombat
 
 D_LIN = np.array([0.1, 0.6, 0.3])
 NH, NIN, NOUT = 32, 6, 3
-
-
-def rotated_state_and_flux(U, gamma, axis):
-    """Rotated conservative 7-vector (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and
-    its physical flux along `axis` (0 x, 1 y, 2 z) for cell arrays U[8, ...]
-    whose B entries hold the cell field."""
-    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
-    rho, E = U[0], U[7]
-    mn, m1, m2 = U[1 + n], U[1 + t1], U[1 + t2]
-    bn, b1, b2 = U[4 + n], U[4 + t1], U[4 + t2]
-    u, v1, v2 = mn / rho, m1 / rho, m2 / rho
-    bb = bn * bn + b1 * b1 + b2 * b2
-    p = (gamma - 1.0) * (E - 0.5 * (mn * u + m1 * v1 + m2 * v2) - 0.5 * bb)
-    pt = p + 0.5 * bb
-    X = np.stack([rho, mn, m1, m2, b1, b2, E])
-    F = np.stack([mn, mn * u + pt - bn * bn, m1 * u - bn * b1, m2 * u - bn * b2,
-                  u * b1 - v1 * bn, u * b2 - v2 * bn, (E + pt) * u - bn * (u * bn + v1 * b1 + v2 * b2)])
-    return X, F
 
 
 def face_reconstruction(f, npaxis):
@@ -68,7 +52,7 @@ def harvest(st, nsamples: int, seed: int = 1808, kappa: float = 4.0, pjump: floa
     nx, ny, nz = st.dims
     out = []
     for axis in axes:
-        X, F = rotated_state_and_flux(st.U, st.gamma, axis)
+        X, F = g.cell_state_flux(axis)
         npax = {0: -1, 1: -2, 2: -3}[axis]
         hX = face_reconstruction(X, npax)
         hF = face_reconstruction(F, npax)

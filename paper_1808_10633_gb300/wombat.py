@@ -27,7 +27,7 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_set_mlp", "wb_autotune", "wb_set_tiles",
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_cell_state_flux", "wb_set_mlp", "wb_autotune", "wb_set_tiles",
            "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals",
            "wb_set_state_f32", "wb_get_state_f32")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
     L.wb_get_state_f32.argtypes = [vp, vp, vp]
     L.wb_step_totals.argtypes = [vp, dp]
     L.wb_harvest.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, d, d, vp]
+    L.wb_cell_state_flux.argtypes = [vp, i, vp, vp]
     L.wb_mlp_loss_grad.argtypes = [vp, ctypes.c_longlong, vp, d, vp, vp]
     L.wb_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, i, i, d, d, ctypes.c_ulonglong, vp]
     L.wb_last_error.restype = ctypes.c_char_p
@@ -303,6 +304,15 @@ class Grid:
         _check(self._lib.wb_harvest(self._h, int(axis), c.ctypes.data, c.size, hu.ctypes.data,
                                     hf.ctypes.data, float(kappa), float(pjump), out.ctypes.data))
         return out
+
+    def cell_state_flux(self, axis: int):
+        """(X, F), each (7, nz, ny, nx): the rotated conservative 7-vector of
+        every cell of patch 0 and its physical flux along `axis`."""
+        nx, ny, nz = self.dims[0]
+        X = np.empty((7, nz, ny, nx))
+        F = np.empty((7, nz, ny, nx))
+        _check(self._lib.wb_cell_state_flux(self._h, int(axis), X.ctypes.data, F.ctypes.data))
+        return X, F
 
     def sync(self):
         _check(self._lib.wb_sync(self._h))

@@ -95,6 +95,36 @@ def _oracle_records(orc, st, axis, cell_ijk, hu, hf, kappa, pjump):
     return out
 
 
+def _oracle_state_flux(orc, st, axis):
+    """Rotated 7-vector and physical flux along `axis` of every cell, from
+    the oracle's cell field (face mean) and its flux function, cell by cell."""
+    nx, ny, nz = st.dims
+    g = orc.Grid(nx, ny, nz, st.dx, st.dy, st.dz, st.gamma)
+    U = orc.cell_b(g, st.U, st.bx, st.by, st.bz)
+    n, t1, t2 = axis, (axis + 1) % 3, (axis + 2) % 3
+    perm = [0, 1 + n, 1 + t1, 1 + t2, 4 + n, 4 + t1, 4 + t2, 7]
+    keep = [0, 1, 2, 3, 5, 6, 7]
+    Ur = U[perm].reshape(8, -1)
+    F = np.empty((7, Ur.shape[1]))
+    for c in range(Ur.shape[1]):
+        F[:, c] = orc.flux_n(Ur[:, c], st.gamma)[keep]
+    return Ur[keep].reshape((7,) + st.U.shape[1:]), F.reshape((7,) + st.U.shape[1:])
+
+
+def test_cell_state_flux_matches_oracle(orc, wb):
+    """wb_cell_state_flux (the sweep's staging arithmetic, row a1) against
+    the oracle's rotated state and flux, every cell, all three axes."""
+    st = I.add_blasts(I.turbulence(16, seed=8), nblast=3, rmin=0.1, rmax=0.15)
+    g = wb.Grid.from_state(st, precision="fp64")
+    for axis in range(3):
+        X, F = g.cell_state_flux(axis)
+        Xo, Fo = _oracle_state_flux(orc, st, axis)
+        for f in range(7):
+            assert np.abs(X[f] - Xo[f]).max() <= 1e-15 * max(np.abs(Xo[f]).max(), 1e-300), (axis, f)
+            assert np.abs(F[f] - Fo[f]).max() <= 1e-13 * max(np.abs(Fo[f]).max(), 1e-300), (axis, f)
+    g.close()
+
+
 def test_harvest_records_match_oracle(orc, wb):
     from paper_1808_10633_gb300 import learned as Ln
 
@@ -105,7 +135,7 @@ def test_harvest_records_match_oracle(orc, wb):
     nx, ny, nz = st.dims
     nflag = 0
     for axis in range(3):
-        X, F = Ln.rotated_state_and_flux(st.U, st.gamma, axis)
+        X, F = _oracle_state_flux(orc, st, axis)
         npax = {0: -1, 1: -2, 2: -3}[axis]
         hX, hF = Ln.face_reconstruction(X, npax), Ln.face_reconstruction(F, npax)
         idx = rng.integers(0, [nx, ny, nz], size=(12, 3))

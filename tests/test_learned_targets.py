@@ -39,12 +39,3 @@ def test_upwind5_converges_to_exact_face_values_at_fifth_order():
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders.min() > 4.7, (errs, orders)
 
-
-def test_rotated_flux_is_frame_consistent():
-    from paper_1808_10633_gb300 import inputs as I
-
-    st = I.perturbed(6, 5, 4, seed=3)
-    for axis in range(3):
-        X, F = Ln.rotated_state_and_flux(st.U, st.gamma, axis)
-        assert X.shape == (7,) + st.shape and np.isfinite(F).all()
-        assert np.allclose(F[0], st.U[1 + axis])           # mass flux = normal momentum
