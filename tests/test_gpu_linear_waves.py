@@ -8,7 +8,7 @@ as Gardiner & Stone (2008) do, amplitude 1e-5.
 * Fast and slow waves: against the linear solution they stop at an N-
   independent floor, the amplitude^2 (steepening) part of the nonlinear
   solution, which falls a hundredfold for a tenfold smaller amplitude;
-  against an N = 512 run of the same nonlinear problem they converge at
+  against an N = 256 run of the same nonlinear problem they converge at
   fifth order over three refinements, to ~1e-11 at N = 64 (the paper:
   WENO5 reaches 1e-11 at 64 zones) and below 1e-12 at N = 128.
 * The GPU errors match the oracle's at N = 32.
@@ -59,7 +59,7 @@ def test_gpu_full_period_fifth_order_to_round_off(wb, mode):
 
 @pytest.mark.parametrize("mode", ["fast", "slow"])
 def test_gpu_self_convergence_fifth_order(wb, mode):
-    NR = 512
+    NR = 256
     ref = _run(wb, mode, NR, offset=0.0)[0]
     errs = [LW.l1_error(_run(wb, mode, N, offset=0.0)[0], ref[..., ::NR // N]) for N in (16, 32, 64, 128)]
     o = _orders(errs)
