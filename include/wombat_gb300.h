@@ -285,9 +285,12 @@ const char *wb_last_error(void);
  * out: device, 8 doubles: totals of (rho, mx, my, mz, Bx, By, Bz, E) * dV.
  * cuda_stream: cudaStream_t to order the work on (NULL: the default stream).
  * Asynchronous: out is valid once the stream has been synchronised.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one scratch array, so
+ * Each call looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with the current device, so a cudaDeviceReset between calls leaves no
+ * stale address; while cuda_stream is being captured the address found by
+ * the last call outside capture on that device is used instead, so make the
+ * first call on a device (and the first after a cudaDeviceReset) before any
+ * stream capture: otherwise WB_EINVAL.  Every call shares the one scratch array, so
  * calls that overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.  Each call rewrites every partial
  * slot it reads, so nothing needs clearing between calls.
