@@ -367,8 +367,22 @@ int wb_cell_state_flux(wb_grid *g, int axis, double *X_out, double *F_out);
  * detector fires the Jiang-Shu weights are used.  Synchronises. */
 int wb_set_mlp(wb_grid *g, const float *params, double kappa, double pjump);
 
-/* Detector log of a WB_FP32_LEARNED grid: out[0] = weight decisions where a
- * detector fired (Jiang-Shu weights used), out[1] = all weight decisions
+/* Smoothness gate of a WB_FP32_LEARNED grid: the networks' weights are used
+ * for a field and side only where its smoothness indicators IS_0..2 (those
+ * of the Jiang-Shu weights, Sec. 2.1, on the four differences phi_N reads)
+ * spread by more than the ratio `smooth`, (eps + max IS) > smooth (eps +
+ * min IS), eps = 1e-6: near critical points of the solution, where the
+ * Jiang-Shu weights lose accuracy.  Where the stencil is smoother than that
+ * the Jiang-Shu weights (within O(dx^2) of the linear weights there) are
+ * kept, so that the network's BF16 rounding does not cap the order of the
+ * scheme on smooth flow.  smooth = 0 (the default): the networks wherever no
+ * detector fires.  Errors: WB_EINVAL (not a learned grid, smooth < 0 or not
+ * finite). */
+int wb_set_mlp_gate(wb_grid *g, double smooth);
+
+/* Detector log of a WB_FP32_LEARNED grid: out[0] = weight decisions that
+ * kept the Jiang-Shu weights (a detector fired, or the smoothness gate of
+ * wb_set_mlp_gate held the network back), out[1] = all weight decisions
  * (7 characteristic fields x 2 sides per interface and sweep), counted on
  * the device over every learned sweep since the grid was made or last
  * reset; reset != 0 zeroes the counters afterwards.  Synchronises.

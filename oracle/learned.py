@@ -133,6 +133,25 @@ def detector(D4, kappa):
     return mx > kappa * others + 1e-300
 
 
+def smoothness_indicators(D4):
+    """IS_0..2 of the Jiang-Shu weights (Sec. 2.1) on the four differences
+    phi_N reads, as printed there."""
+    a, b, c, d = (float(v) for v in D4)
+    return (13.0 * (a - b) ** 2 + 3.0 * (a - 3.0 * b) ** 2,
+            13.0 * (b - c) ** 2 + 3.0 * (b + c) ** 2,
+            13.0 * (c - d) ** 2 + 3.0 * (3.0 * c - d) ** 2)
+
+
+def rough(D4, smooth, eps=1e-6):
+    """The smoothness gate: the network's weights are used only where the
+    smoothness indicators spread by more than the ratio `smooth`,
+    (eps + max IS) > smooth (eps + min IS); returns (decision, relative
+    distance from the threshold)."""
+    IS = smoothness_indicators(D4)
+    lhs, rhs = eps + max(IS), smooth * (eps + min(IS))
+    return lhs > rhs, abs(lhs - rhs) / max(rhs, lhs, 1e-300)
+
+
 def phi_n_weights(a, b, c, d, w0, w2):
     return w0 * (a - 2 * b + c) / 3.0 + (w2 - 0.5) * (b - 2 * c + d) / 6.0
 
@@ -150,12 +169,14 @@ def linear_params():
     return pack(W1, b1, W2, b2, W3, b3)
 
 
-def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5, margins=None):
+def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5, margins=None, smooth=0.0):
     """Eq. FWENO flux at i+1/2 (rotated frame, stencil cells i-2..i+3, 6x8)
     with the Jiang-Shu weights replaced by the network's (params: 7 x 1379)
     wherever neither detector fires: the jump detector on the side's four
     differences, or a pressure ratio max p / min p > 1 + pjump over the six
-    cells (then every field falls back to Jiang-Shu).  Same steps as the
+    cells (then every field falls back to Jiang-Shu); and, with smooth > 0,
+    only where the side's smoothness indicators spread by more than the
+    ratio `smooth` (see `rough`).  Same steps as the
     oracle's orc_interface_flux otherwise.  With a list `margins`, the
     smallest relative distance of any detector input from its threshold is
     appended to it (how far the decisions are from flipping)."""
@@ -192,7 +213,10 @@ def interface_flux_learned(Us, gamma, params, kappa=4.0, pjump=0.5, margins=None
             a = np.abs(D)
             thr = kappa * (a.sum() - a.max()) / 3.0
             margin = min(margin, abs(a.max() - thr) / (thr + 1e-300))
-            if pfire or detector(D, kappa):
+            use_net, m_s = rough(D, smooth)
+            if smooth > 0.0:
+                margin = min(margin, m_s)
+            if pfire or detector(D, kappa) or not use_net:
                 out.append(O.phi_n(*D))
             else:
                 om, _ = forward(params[s], normalise(v))

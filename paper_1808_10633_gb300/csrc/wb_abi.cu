@@ -92,7 +92,7 @@ struct wb_grid {
     int step_totals = 0;                  // 1: every step also takes the totals of its start state
     cudaStream_t side = nullptr;          // stream the per-step totals run on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    double kappa = 4.0, pjump = 0.5;
+    double kappa = 4.0, pjump = 0.5, smooth = 0.0;
     int tile_policy[3] = {-2, -2, -2};    // build_tiles policy of each axis' table
     int tile_split[3][3] = {};            // per axis: tiles of each shape of a table sorted
                                           // by shape, or all 0 (wb::SweepArgs::split)
@@ -177,7 +177,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             if constexpr (sizeof(T) == 4) {
                 if (g->precision == WB_FP32_LEARNED)
                     WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
-                                                   (float)g->pjump, g->stream));
+                                                   (float)g->pjump, (float)g->smooth, g->stream));
                 else
                     WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
             } else {
@@ -521,7 +521,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
         if (g->precision == WB_FP32_LEARNED) {
             if (!g->d_mlp) return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
             WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
-                                           (float)g->pjump, g->stream));
+                                           (float)g->pjump, (float)g->smooth, g->stream));
         } else {
             WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
         }
@@ -1030,6 +1030,19 @@ int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
     WB_CK(cudaStreamSynchronize(g->stream));
     g->kappa = kappa;
     g->pjump = pjump;
+    if (g->graph) {              // kernel arguments changed: capture again
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    return WB_OK;
+}
+
+int wb_set_mlp_gate(wb_grid* g, double smooth) {
+    g_err.clear();
+    if (!g) return fail(WB_EINVAL, "null grid");
+    if (g->precision != WB_FP32_LEARNED) return fail(WB_EINVAL, "wb_set_mlp_gate needs a WB_FP32_LEARNED grid");
+    if (!(smooth >= 0) || !(smooth < 1e30)) return fail(WB_EINVAL, "smooth must be >= 0 and finite");
+    g->smooth = smooth;
     if (g->graph) {              // kernel arguments changed: capture again
         cudaGraphExecDestroy(g->graph);
         g->graph = nullptr;

@@ -200,7 +200,7 @@ int update_vector_width(bool fp64);
 
 cudaError_t prepare_sweep_learned();
 cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles, const uint32_t* mlp,
-                                 float kappa, float pjump, cudaStream_t s);
+                                 float kappa, float pjump, float smooth, cudaStream_t s);
 void mlp_fragments(const float* params, uint32_t* out);
 size_t mlp_fragment_words();
 

@@ -890,8 +890,26 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T>& A, const Tile& til
 }
 
 // Persistent sweep: a grid of (SMs x resident blocks) strides over the tile
-// table; each tile carries its shape, read by one body with the shape as a
-// block-uniform runtime value, so patches of uneven sizes share one launch.
+// table; each tile carries its shape, so patches of uneven sizes share one
+// launch.  Each tile runs the body compiled for its shape (a block-uniform
+// switch over the three shapes, so every body keeps its compile-time
+// layout); WB_SWEEP_PERSIST_SWITCH=0 selects one body with the shape as a
+// runtime value instead.
+#ifndef WB_SWEEP_PERSIST_SWITCH
+#define WB_SWEEP_PERSIST_SWITCH 1
+#endif
+// One shape's body; WB_SWEEP_PERSIST_SWITCH=2 keeps it out of line, so that
+// each of the three bodies gets a register allocation of its own.
+#if WB_SWEEP_PERSIST_SWITCH == 2
+#define WB_SHAPE_INLINE __noinline__
+#else
+#define WB_SHAPE_INLINE __forceinline__
+#endif
+template <class T, int AXIS, int S, int NCMAX, bool Z>
+__device__ WB_SHAPE_INLINE void tile_body_shape(const SweepArgs<T>& A, const Tile& tile, const PatchDev& P,
+                                                T* __restrict__ sm, int tid) {
+    tile_body<T, AXIS, shape_ta(AXIS, S), NCMAX, Z>(A, tile, P, sm, tid);
+}
 template <class T, int AXIS, bool Z>
 __global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel(const SweepArgs<T> A, int ntiles) {
     constexpr int NCMAX = max_nc(AXIS);
@@ -907,7 +925,13 @@ __global__ void __launch_bounds__(kSweepNT, MinBlocks<T>::value) sweep_kernel(co
         const int shape = (unsigned)tile.x >> 24;
         tile.x &= 0xffffff;
         const PatchDev P = A.patches[tile.x];
+#if WB_SWEEP_PERSIST_SWITCH
+        if (shape == 0) tile_body_shape<T, AXIS, 0, NCMAX, Z>(A, tile, P, sm, tid);
+        else if (shape == 1) tile_body_shape<T, AXIS, 1, NCMAX, Z>(A, tile, P, sm, tid);
+        else tile_body_shape<T, AXIS, 2, NCMAX, Z>(A, tile, P, sm, tid);
+#else
         tile_body<T, AXIS, 0, NCMAX, Z>(A, tile, P, sm, tid, shape_ta(AXIS, shape));
+#endif
         __syncthreads();
         if (A.queue) {
             if (tid == 0) next_tile = gridDim.x + atomicAdd(A.queue, 1);

@@ -170,7 +170,19 @@ struct LearnedWeights {
     int lane;
     bool pfire;               // pressure detector of this interface
     float kappa;
-    int nfire = 0;            // detector firings of this thread (fields x sides)
+    float smooth;             // network only where (eps + max IS) > smooth (eps + min IS)
+    int nfire = 0;            // Jiang-Shu decisions of this thread (fields x sides)
+
+    // The smoothness gate: true where the smoothness indicators of phi_N's
+    // four differences (Sec. 2.1) spread by more than `smooth`.
+    __device__ __forceinline__ bool rough(float a, float b, float c, float d) const {
+        const float t0 = a - b, t1 = a - 3.0f * b, t2 = b - c, t3 = b + c, t4 = c - d, t5 = 3.0f * c - d;
+        const float is0 = 13.0f * t0 * t0 + 3.0f * t1 * t1;
+        const float is1 = 13.0f * t2 * t2 + 3.0f * t3 * t3;
+        const float is2 = 13.0f * t4 * t4 + 3.0f * t5 * t5;
+        const float mx = fmaxf(is0, fmaxf(is1, is2)), mn = fminf(is0, fminf(is1, is2));
+        return mx + 1e-6f > smooth * (mn + 1e-6f);
+    }
 
     __device__ __forceinline__ float corr(int s, const float (&w)[6], const float (&g)[6], float alpha) {
 #if WB_LEARNED_PACKED
@@ -210,7 +222,8 @@ struct LearnedWeights {
             float a[4], dmax = 0.f, dsum = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; k++) { a[k] = fabsf(D[k]); dmax = fmaxf(dmax, a[k]); dsum += a[k]; }
-            fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f;
+            fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f
+                         || !rough(D[0], D[1], D[2], D[3]);
             nfire += fire[side] ? 1 : 0;
         }
         __syncwarp();
@@ -275,7 +288,21 @@ struct LearnedWeights {
                 dsum += a;
             }
             fire[side] = pfire || dmax > kappa * (dsum - dmax) * (1.0f / 3.0f) + 1e-30f;
-            nfire += fire[side] ? 1 : 0;
+        }
+        {
+            // smoothness gate on both sides at once (the indicators are even
+            // in D, so lane y's negated differences give the '-' side's)
+            const float2 t0 = __ffma2_rn(D[1], splat2(-1.0f), D[0]), t1 = __ffma2_rn(D[1], splat2(-3.0f), D[0]);
+            const float2 t2 = __ffma2_rn(D[2], splat2(-1.0f), D[1]), t3 = __fadd2_rn(D[1], D[2]);
+            const float2 t4 = __ffma2_rn(D[3], splat2(-1.0f), D[2]), t5 = __ffma2_rn(D[2], splat2(3.0f), __fmul2_rn(D[3], splat2(-1.0f)));
+            const float2 is0 = __ffma2_rn(__fmul2_rn(t0, splat2(13.0f)), t0, __fmul2_rn(__fmul2_rn(t1, splat2(3.0f)), t1));
+            const float2 is1 = __ffma2_rn(__fmul2_rn(t2, splat2(13.0f)), t2, __fmul2_rn(__fmul2_rn(t3, splat2(3.0f)), t3));
+            const float2 is2 = __ffma2_rn(__fmul2_rn(t4, splat2(13.0f)), t4, __fmul2_rn(__fmul2_rn(t5, splat2(3.0f)), t5));
+            const float mxp = fmaxf(is0.x, fmaxf(is1.x, is2.x)), mnp = fminf(is0.x, fminf(is1.x, is2.x));
+            const float mxm = fmaxf(is0.y, fmaxf(is1.y, is2.y)), mnm = fminf(is0.y, fminf(is1.y, is2.y));
+            fire[0] = fire[0] || !(mxp + 1e-6f > smooth * (mnp + 1e-6f));
+            fire[1] = fire[1] || !(mxm + 1e-6f > smooth * (mnm + 1e-6f));
+            nfire += (fire[0] ? 1 : 0) + (fire[1] ? 1 : 0);
         }
         __syncwarp();
         mlp_warp(W + s * kMlpWords * 32, in, om, lane);
@@ -300,7 +327,7 @@ struct LearnedWeights {
 template <int AXIS>
 __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(const SweepArgs<float> A,
                                                                const uint32_t* __restrict__ mlp,
-                                                               float kappa, float pjump) {
+                                                               float kappa, float pjump, float smooth) {
     using T = float;
     constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
     constexpr int NS = TA + 5;
@@ -366,7 +393,7 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     }
     const int lane = tid & 31, warp = tid >> 5;
     LearnedWeights lw{Wsm, wbuf + warp * 384, reinterpret_cast<float*>(wbuf + warp * 384 + 256), lane,
-                      pmax > (1.0f + pjump) * pmin, kappa};
+                      pmax > (1.0f + pjump) * pmin, kappa, smooth};
     T F[7];
     T* bp = sm + kNSlot * NC + tid;
     interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, lw, F);
@@ -427,17 +454,17 @@ cudaError_t prepare_sweep_learned() {
 }
 
 cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles, const uint32_t* mlp,
-                                 float kappa, float pjump, cudaStream_t s) {
+                                 float kappa, float pjump, float smooth, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (axis == 0)
         sweep_learned_kernel<0><<<ntiles, dim3(Shape<0>::TA, Shape<0>::TP), learned_smem_bytes<0>(), s>>>(
-            a, mlp, kappa, pjump);
+            a, mlp, kappa, pjump, smooth);
     else if (axis == 1)
         sweep_learned_kernel<1><<<ntiles, dim3(Shape<1>::TP, Shape<1>::TA), learned_smem_bytes<1>(), s>>>(
-            a, mlp, kappa, pjump);
+            a, mlp, kappa, pjump, smooth);
     else
         sweep_learned_kernel<2><<<ntiles, dim3(Shape<2>::TP, Shape<2>::TA), learned_smem_bytes<2>(), s>>>(
-            a, mlp, kappa, pjump);
+            a, mlp, kappa, pjump, smooth);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ INTEGRATORS = {"ssprk3": WB_SSPRK3, "rk4": WB_RK4}
 EXPORTS = ("wb_init_grid", "wb_set_state", "wb_step", "wb_step_cfl", "wb_cfl_dt",
            "wb_conserved_totals", "wb_get_state", "wb_sync", "wb_get_info", "wb_destroy",
            "wb_last_error", "wb_version", "wb_step_profiled", "wb_alu_peak", "wb_face_fluxes",
-           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_cell_state_flux", "wb_set_mlp", "wb_autotune", "wb_set_tiles",
+           "wb_conserved_totals_noalloc", "wb_mlp_loss_grad", "wb_mlp_train", "wb_harvest", "wb_cell_state_flux", "wb_set_mlp", "wb_set_mlp_gate", "wb_autotune", "wb_set_tiles",
            "wb_learned_stats", "wb_div_b", "wb_set_step_totals", "wb_step_totals",
            "wb_set_state_f32", "wb_get_state_f32")
 MLP_NFIELD, MLP_NPARAM, MLP_RECORD = 7, 1379, 12
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
     L.wb_face_fluxes.argtypes = [vp, i, vp]
     L.wb_conserved_totals_noalloc.argtypes = [vp, i, ctypes.c_longlong, d, vp, vp]
     L.wb_set_mlp.argtypes = [vp, vp, d, d]
+    L.wb_set_mlp_gate.argtypes = [vp, d]
     L.wb_autotune.argtypes = [vp, vp]
     L.wb_set_tiles.argtypes = [vp, ctypes.c_int]
     L.wb_learned_stats.argtypes = [vp, vp, i]
@@ -283,13 +284,22 @@ class Grid:
         TILE_CANDIDATES) without timing it."""
         _check(self._lib.wb_set_tiles(self._h, int(candidate)))
 
-    def set_mlp(self, params, kappa: float = 4.0, pjump: float = 0.5):
-        """Install the learned-weight networks (7 x 1379 floats)."""
+    def set_mlp(self, params, kappa: float = 4.0, pjump: float = 0.5, smooth: float | None = None):
+        """Install the learned-weight networks (7 x 1379 floats); `smooth`
+        sets the smoothness gate (wb_set_mlp_gate) as well."""
         p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_NFIELD * MLP_NPARAM)
         _check(self._lib.wb_set_mlp(self._h, p.ctypes.data, float(kappa), float(pjump)))
+        if smooth is not None:
+            self.set_mlp_gate(smooth)
+
+    def set_mlp_gate(self, smooth: float):
+        """Use the networks only where the smoothness indicators spread by
+        more than the ratio `smooth` (0: wherever no detector fires)."""
+        _check(self._lib.wb_set_mlp_gate(self._h, float(smooth)))
 
     def learned_stats(self, reset: bool = False):
-        """(detector firings, weight decisions) counted by the learned sweeps."""
+        """(decisions that kept the Jiang-Shu weights, all weight decisions)
+        counted by the learned sweeps."""
         out = (ctypes.c_longlong * 2)()
         _check(self._lib.wb_learned_stats(self._h, out, int(bool(reset))))
         return int(out[0]), int(out[1])

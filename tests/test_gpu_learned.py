@@ -177,11 +177,16 @@ def _bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _sample_learned_fluxes(orc, wb, st, params, kappa, pjump, nsamp, seed, bf16_params=True):
+def _sample_learned_fluxes(orc, wb, st, params, kappa, pjump, nsamp, seed, bf16_params=True, smooth=None,
+                           min_margin=0.0):
+    """GPU face fluxes of a learned grid at sampled interfaces and the FP64
+    reference's; samples whose nearest decision is closer than min_margin
+    (relative) to its threshold are left out (FP32 and FP64 may take either
+    side there)."""
     from oracle import learned as Lr
 
     g = wb.Grid.from_state(st, precision="learned")
-    g.set_mlp(params, kappa, pjump)
+    g.set_mlp(params, kappa, pjump, smooth=smooth)
     rng = np.random.default_rng(seed)
     nx, ny, nz = st.dims
     P = _bf16(params) if bf16_params else np.asarray(params, np.float64)
@@ -205,7 +210,11 @@ def _sample_learned_fluxes(orc, wb, st, params, kappa, pjump, nsamp, seed, bf16_
                 q = [i, j, k]
                 q[axis] = (q[axis] + m - 3) % (nx, ny, nz)[axis]
                 Us[m] = st.U[perm, q[2], q[1], q[0]]
-            Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump)
+            margins = []
+            Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump, margins=margins,
+                                           smooth=smooth or 0.0)
+            if margins[0] < min_margin:
+                continue
             r = np.empty(7)
             r[0] = Fh[0]
             for gq in range(3):
@@ -252,6 +261,33 @@ def test_learned_sweep_random_network_matches_oracle(orc, wb):
     ln = np.concatenate([lg.face_fluxes(a)[:, :1] for a in range(3)], axis=1)
     lg.close()
     assert np.abs(ln - js).max() / np.abs(js).max() > 10 * err
+
+
+def test_learned_sweep_smoothness_gate_matches_oracle(orc, wb):
+    """With the smoothness gate (network only where the smoothness indicators
+    spread by more than 5 %) a random network's fluxes match the FP64
+    reference taking the same decisions; with the gate shut everywhere the
+    learned sweep gives the Jiang-Shu fluxes."""
+    rng = np.random.default_rng(14)
+    from oracle import learned as Lr
+
+    params = (rng.standard_normal((7, Lr.NPARAM)) * 0.5).astype(np.float32)
+    st = I.turbulence(24, seed=35)
+    got, ref = _sample_learned_fluxes(orc, wb, st, params, 1e30, 1e30, 60, 3, smooth=1.05, min_margin=1e-2)
+    assert len(got) >= 100
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-3 * np.abs(ref).max())
+    assert (np.abs(got - ref) / scale).max() < 5e-3
+    g = wb.Grid.from_state(st, precision="fp32")
+    lg = wb.Grid.from_state(st, precision="learned")
+    lg.set_mlp(params, 1e30, 1e30, smooth=1e29)
+    for a in range(3):
+        F1, F2 = g.face_fluxes(a), lg.face_fluxes(a)
+        assert np.abs(F1 - F2).max() <= 1e-6 * np.abs(F1).max()
+    lg.step(1e-3, 1)
+    fired, n = lg.learned_stats()
+    assert fired == n > 0
+    g.close()
+    lg.close()
 
 
 def test_learned_sweep_detector_falls_back_to_js(wb):

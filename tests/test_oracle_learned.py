@@ -86,6 +86,45 @@ def test_detector_fires_on_jumps_not_on_smooth_extrema():
     assert not Lr.detector(np.zeros((1, 4)), 4.0)[0]
 
 
+def test_smoothness_gate():
+    """The gate reads the Jiang-Shu smoothness indicators of Sec. 2.1.  On
+    linear data all three equal 12 a^2 (no spread: the network is held back
+    for any ratio above 1).  Near a critical point of the flux in general
+    position they differ by O(h) relatively, on a monotone smooth stretch by
+    O(h^2) (Henrick et al. 2005): the spread a ratio just above 1 tells
+    apart."""
+    a = 0.37
+    assert Lr.smoothness_indicators([a, a, a, a]) == pytest.approx((12 * a * a,) * 3, rel=1e-15)
+    assert not Lr.rough([a] * 4, 1.01)[0] and Lr.rough([a] * 4, 0.99)[0]
+    spread = lambda D: max(Lr.smoothness_indicators(D)) / min(Lr.smoothness_indicators(D)) - 1.0
+    # f = x^2 + x^3: a critical point at 0 with a nonzero third derivative
+    # there (the O(h) term needs it); stencil off-centre by 0.3 h
+    ext = [np.diff(((np.arange(-2, 3) + 0.3) * h) ** 2 + ((np.arange(-2, 3) + 0.3) * h) ** 3)
+           for h in (0.04, 0.02)]
+    mono = [np.diff(np.sin(0.7 + np.arange(-2, 3) * h) + 0.5 * (0.7 + np.arange(-2, 3) * h))
+            for h in (0.04, 0.02)]
+    assert 1.7 < spread(ext[0]) / spread(ext[1]) < 2.3             # O(h)
+    assert 3.4 < spread(mono[0]) / spread(mono[1]) < 4.6           # O(h^2)
+    assert Lr.rough(ext[1], 1.01)[0] and not Lr.rough(mono[1], 1.01)[0]
+    assert Lr.rough(mono[1], 0.0)[0]
+
+
+def test_gate_shut_gives_the_jiang_shu_flux(orc):
+    """smooth above every spread: the learned reference is the oracle's
+    Jiang-Shu flux (same steps, numpy instead of C)."""
+    rng = np.random.default_rng(4)
+    gam = 5.0 / 3.0
+    P = rng.standard_normal((7, Lr.NPARAM)) * 0.5
+    for t in range(5):
+        W = [[1.0 + 0.1 * rng.random(), 0.2 * rng.standard_normal(), 0.2 * rng.standard_normal(),
+              0.2 * rng.standard_normal(), 0.8, 0.3 * rng.standard_normal(), 0.3 * rng.standard_normal(),
+              0.6 + 0.1 * rng.random()] for _ in range(6)]
+        Us = np.array([orc.prim_to_cons(w, gam) for w in W])
+        F = Lr.interface_flux_learned(Us, gam, P, kappa=1e30, pjump=1e30, smooth=1e300)
+        Fj = orc.interface_flux(Us, gam)
+        assert np.abs(F - Fj).max() <= 1e-13 * np.abs(Fj).max()
+
+
 def test_learned_flux_with_linear_network_matches_upwind_on_entropy_wave(orc):
     """With omega = d and the detector off, a decoupled entropy wave's mass
     flux is the linear upwind-5 combination of u*rho."""
