@@ -204,12 +204,42 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
     }
 }
 
+// The same correction from the projected differences of the stencil,
+// dw_m = l_s (U_{m+1} - U_m), dg_m = l_s (F_{m+1} - F_m), m = 0..4 (the
+// projection is linear, so D+-_{m+1/2} = (dg_m +- alpha dw_m) / 2).
+template <class T, bool Z = false>
+__device__ __forceinline__ T weno_corr_d(const T (&dw)[5], const T (&dg)[5], T alpha) {
+    const T ha = T(0.5) * alpha;
+    T hg[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) hg[m] = T(0.5) * dg[m];
+    const T dp0 = hg[0] + ha * dw[0], dp1 = hg[1] + ha * dw[1], dp2 = hg[2] + ha * dw[2], dp3 = hg[3] + ha * dw[3];
+    const T dm1 = hg[1] - ha * dw[1], dm2 = hg[2] - ha * dw[2], dm3 = hg[3] - ha * dw[3], dm4 = hg[4] - ha * dw[4];
+    if constexpr (Z && WB_SWEEP_PACKED && sizeof(T) == 4) {
+        const float2 ph = phi_n_z2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
+                                   make_float2(dm1, dp3));
+        return ph.x - ph.y;
+    } else if constexpr (Z) {
+        return phi_n_z(dm4, dm3, dm2, dm1) - phi_n_z(dp0, dp1, dp2, dp3);
+    } else if constexpr (WB_SWEEP_PACKED && sizeof(T) == 4) {
+        const float2 ph = phi_n2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
+                                 make_float2(dm1, dp3));
+        return ph.x - ph.y;
+    } else {
+        return phi_n(dm4, dm3, dm2, dm1) - phi_n(dp0, dp1, dp2, dp3);
+    }
+}
+
 // Weight policy of the classic scheme: Jiang-Shu weights for every field,
 // or the WENO-Z weights when Z is set (a separate kernel instance).
 template <class T, bool Z = false>
 struct JsWeights {
+    static constexpr bool kDiff = true;      // works on projected differences
     __device__ __forceinline__ T corr(int, const T (&w)[6], const T (&g)[6], T alpha) {
         return weno_corr<T, Z>(w, g, alpha);
+    }
+    __device__ __forceinline__ T corr_d(int, const T (&dw)[5], const T (&dg)[5], T alpha) {
+        return weno_corr_d<T, Z>(dw, dg, alpha);
     }
 };
 
@@ -227,8 +257,12 @@ struct Eig {
 // slot per thread) while the WENO step runs, to keep registers for it.
 enum : int { BP_ALF = 0, BP_ALS, BP_AFCF, BP_ASCS, BP_ASR, BP_SSR, BP_RA2, BP_IGM1, kNBack = 8 };
 // Per-thread slots after the back-projection ones where the Alfven/entropy
-// projections (3 fields x (w, g) x 6 cells) wait while the fast/slow group
-// is reconstructed, when each stencil vector is projected only once.
+// projections (3 fields x (w, g) x 6 cells, or x 5 differences) wait while
+// the fast/slow group is reconstructed, when each stencil vector is
+// projected only once.
+#ifndef WB_SWEEP_DELTA
+#define WB_SWEEP_DELTA 1               // 1: project the stencil's differences (PARK path)
+#endif
 constexpr int kNPark = 36;
 constexpr int kNThreadSlots = kNBack + (WB_SWEEP_PARK ? kNPark : 0);
 
@@ -631,7 +665,56 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         }
     }
 #else
-    if constexpr (PARK) {
+    if constexpr (PARK && WB_SWEEP_DELTA && Wt::kDiff) {
+        // 3. the five differences of the stencil's U and F, each projected
+        // once onto all seven fields; the Alfven/entropy values wait in
+        // this thread's shared-memory slots
+        T* park = bp + kNBack * bstride;
+        T dw[4][5], dg[4][5];
+        T u0[7], f0[7];
+        load7(sm, nc, SU, id[0], u0);
+        load7(sm, nc, SF, id[0], f0);
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            T u1[7], f1[7], x[7], o4[4], o3[3];
+            load7(sm, nc, SU, id[m + 1], u1);
+#pragma unroll
+            for (int f = 0; f < 7; f++) x[f] = u1[f] - u0[f];
+            project_all(e, x, o4, o3);
+#pragma unroll
+            for (int f = 0; f < 4; f++) dw[f][m] = o4[f];
+#pragma unroll
+            for (int f = 0; f < 3; f++) park[(f * 5 + m) * bstride] = o3[f];
+            load7(sm, nc, SF, id[m + 1], f1);
+#pragma unroll
+            for (int f = 0; f < 7; f++) x[f] = f1[f] - f0[f];
+            project_all(e, x, o4, o3);
+#pragma unroll
+            for (int f = 0; f < 4; f++) dg[f][m] = o4[f];
+#pragma unroll
+            for (int f = 0; f < 3; f++) park[((3 + f) * 5 + m) * bstride] = o3[f];
+#pragma unroll
+            for (int f = 0; f < 7; f++) { u0[f] = u1[f]; f0[f] = f1[f]; }
+        }
+        // 4-5. fast and slow fields
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+            const int s = 2 * f;
+            corr[s] = wt.corr_d(s, dw[f], dg[f], lf_speed(sm, nc, id, s, lam_avg(e, s)));
+        }
+        // 4-5. Alfven and entropy fields
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            T wa[5], ga[5];
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                wa[m] = park[(f * 5 + m) * bstride];
+                ga[m] = park[((3 + f) * 5 + m) * bstride];
+            }
+            const int s = 2 * f + 1;
+            corr[s] = wt.corr_d(s, wa, ga, lf_speed(sm, nc, id, s, lam_avg(e, s)));
+        }
+    } else if constexpr (PARK) {
         // 3. each stencil vector projected once onto all seven fields; the
         // Alfven/entropy values wait in this thread's shared-memory slots
         T* park = bp + kNBack * bstride;

@@ -164,6 +164,7 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
 
 // Weight policy of the learned scheme.
 struct LearnedWeights {
+    static constexpr bool kDiff = false;     // works on the stencil values themselves
     const uint32_t* W;        // shared, [field][34][32]
     uint32_t* in;             // shared, this warp's 64 x 4 words
     float* om;                // shared, this warp's 64 x 2
