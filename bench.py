@@ -36,8 +36,11 @@ UNIT = "zone-updates/s"
 
 # Algorithmic FP operations of one interface of the sweep kernel (one
 # direction, one stage) and of one staged cell, counted from the kernel's
-# formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1).
-SWEEP_FLOPS_PER_INTERFACE = 2040
+# formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1): eigen-structure 100,
+# interface average 16, central flux 35, differences of the stencil 70,
+# their projection 10 x 68, split differences and two phi_N per field
+# 7 x 125, back-projection 80.
+SWEEP_FLOPS_PER_INTERFACE = 1856
 SWEEP_FLOPS_PER_STAGED_CELL = 80
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -311,6 +314,7 @@ def run_native(args, rank, world, local):
     # ---- learned weights on turbulence + blasts (config 5) -----------------
     learned = None
     if not args.no_learned:
+        args.sm_mhz = clk.get("sm_mhz")
         learned = run_learned(args, st, world, peak32)
 
     # ---- end to end through the ABI with pinned host buffers --------------
@@ -491,17 +495,32 @@ def bf16_peak_tflops():
         return 1700.0, "fallback (1.7 PFLOP/s sustained)"
 
 
-def learned_roofline(n, cls, ms_launch, mlp_flops, peak32):
+# Special-function (MUFU) operations per interface of the learned sweep: the
+# GELU takes one hardware tanh per BF16 pair (14 network evaluations x 2
+# hidden layers x 16 pairs), the softmax three exponentials and a reciprocal
+# per evaluation, the input normalisation one reciprocal per evaluation.
+LEARNED_SFU_PER_INTERFACE = 14 * 2 * 16 + 14 * 4 + 14
+SFU_OPS_PER_CLK_PER_SM = 16          # 4 per SM sub-partition
+
+
+def learned_roofline(n, cls, ms_launch, mlp_flops, peak32, sm_mhz, nsm):
     """Roofline time of one learned sweep launch: the Jiang-Shu part of the
     sweep at the FP32 FMA peak plus the networks at the BF16 tensor peak
-    (additive), against the measured launch time."""
+    (additive), against the measured launch time; beside it the same with
+    the GELU's special-function operations at the MUFU rate (unit count x
+    the SM clock seen during the run)."""
     iface, staged = sweep_units(n)
     alu_flops = iface * SWEEP_FLOPS_PER_INTERFACE + staged[cls] * SWEEP_FLOPS_PER_STAGED_CELL
     bf16, src = bf16_peak_tflops()
     t_roof = alu_flops / (peak32 * 1e12) + mlp_flops / (bf16 * 1e12)
+    sfu_rate = SFU_OPS_PER_CLK_PER_SM * nsm * sm_mhz * 1e6
+    t_sfu = iface * LEARNED_SFU_PER_INTERFACE / sfu_rate
     return {"bound": "alu+tensor", "ms_per_launch": round(ms_launch, 4),
             "ms_at_peaks": round(t_roof * 1e3, 4), "frac": round(t_roof * 1e3 / ms_launch, 4),
-            "fp32_peak_tflops": round(peak32, 3), "bf16_peak_tflops": bf16, "bf16_peak_source": src}
+            "fp32_peak_tflops": round(peak32, 3), "bf16_peak_tflops": bf16, "bf16_peak_source": src,
+            "sfu_ms_at_peak": round(t_sfu * 1e3, 4),
+            "frac_with_sfu": round((t_roof + t_sfu) * 1e3 / ms_launch, 4),
+            "sfu_peak_source": f"{SFU_OPS_PER_CLK_PER_SM} MUFU ops/clk/SM x {nsm} SMs x {sm_mhz:.0f} MHz"}
 
 
 def _l1(U, ref):
@@ -530,7 +549,7 @@ def run_learned(args, st, world, peak32):
     n = args.size
     zones = n ** 3
     gl = wombat.Grid.from_state(st5, precision="learned", stream=cur_stream().cuda_stream)
-    gl.set_mlp(params, 4.0, 0.5)
+    gl.set_mlp(params, 4.0, 0.5, smooth=args.smooth)
     gl.set_step_totals(True)
     gl.step_cfl(args.cfl, args.warmup)
     gl.learned_stats(reset=True)
@@ -544,15 +563,27 @@ def run_learned(args, st, world, peak32):
     mlp_flops = 14 * 2 * (6 * 32 + 32 * 32 + 32 * 3) * zones
     cls = max(("sweep_x", "sweep_y", "sweep_z"), key=lambda k: kms[k])
     ms_l = kms[cls] / max(kcnt[cls], 1)
-    res = {"workload": f"turbulence {n}^3 + 64 blast spheres (p x100, r 0.02-0.05), learned weights",
+    props = torch.cuda.get_device_properties(0)
+    sm_mhz = float(getattr(args, "sm_mhz", None) or 2070.0)
+    res = {"workload": f"turbulence {n}^3 + 64 blast spheres (p x100, r 0.02-0.05), learned weights "
+                       f"(smoothness gate {args.smooth})",
            "value": value, "unit": UNIT, "ms_per_step": secs * 1e3 / args.steps,
            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "train": {"records": int(rec.shape[0]), "unflagged": int((rec[:, 11] == 0).sum()),
                      "steps": 1500, "harvest_s": t_h, "train_s": t_t,
                      "loss_first": float(hist[:20].mean()), "loss_last": float(hist[-20:].mean())},
            "sweep_mlp_tflops": mlp_flops / (ms_l * 1e-3) / 1e12,
-           "roofline": learned_roofline(n, cls, ms_l, mlp_flops, peak32),
-           "detector_fire_rate": fired / max(decisions, 1), "weight_decisions": decisions}
+           "roofline": learned_roofline(n, cls, ms_l, mlp_flops, peak32, sm_mhz, props.multi_processor_count),
+           "js_weight_rate": fired / max(decisions, 1), "weight_decisions": decisions}
+    # what the networks gain: Alfven-wave L1 error against the exact solution
+    gain = Ln.alfven_gain(params, Ns=(16, 32, 64), smooth=args.smooth)
+    res["gain_vs_js"] = {str(N): round(g["vs_js"], 4) for N, g in gain.items()}
+    res["gain_vs_weno_z"] = {str(N): round(g["vs_weno_z"], 4) for N, g in gain.items()}
+    res["gain_l1"] = {str(N): {k: g[k] for k in ("learned", "js", "weno_z", "js_decisions")}
+                      for N, g in gain.items()}
+    res["gain_workload"] = ("circularly polarised Alfven wave, amplitude 0.1, N x 1 x 1, t = 0.2, "
+                            "L1 of B_y against the exact solution; ratios learned / Jiang-Shu and "
+                            "learned / WENO-Z, all FP32")
     if args.l1_steps > 0:
         nst = max(1, args.l1_steps // 2)
         b5 = np.stack([st5.bx, st5.by, st5.bz])
@@ -657,6 +688,8 @@ def main():
     ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--patches", type=int, default=4096,
                     help="patch count of the batched-patch leg (0: skip)")
+    ap.add_argument("--smooth", type=float, default=1.02,
+                    help="smoothness gate of the learned weights (wb_set_mlp_gate)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")
     ap.add_argument("--out-dir", default=os.environ.get("WB_BENCH_OUT"),
