@@ -87,3 +87,37 @@ def train(records, params=None, steps: int = 2000, batch: int = 4096, lr: float 
     if params is None:
         params = init_params(seed)
     return wombat.mlp_train(records, params, steps, batch, lr, lam, seed)
+
+
+def alfven_gain(params, Ns=(16, 32, 64), T: float = 0.2, kappa: float = 4.0, pjump: float = 0.5,
+                smooth: float | None = None):
+    """What the networks gain: the L1 error of B_y against the exact
+    travelling solution of the circularly polarised Alfven wave (amplitude
+    0.1, along x, N x 1 x 1 cells) at time T, for the learned weights and,
+    on FP32 grids of the same resolution, the Jiang-Shu and WENO-Z weights.
+    Returns {N: {"learned", "js", "weno_z", "vs_js", "vs_weno_z",
+    "js_decisions"}} (js_decisions: fraction of weight decisions that kept
+    the Jiang-Shu weights)."""
+    from . import inputs
+
+    out = {}
+    for N in Ns:
+        errs = {}
+        for name, prec, weights in (("learned", "learned", "js"), ("js", "fp32", "js"), ("weno_z", "fp32", "z")):
+            st = inputs.alfven_wave(N, 1, 1, amp=0.1)
+            g = wombat.Grid.from_state(st, precision=prec, weights=weights)
+            if prec == "learned":
+                g.set_mlp(params, kappa, pjump, smooth=smooth)
+            n = int(np.ceil(T / (0.4 / (3 * 1.2 * N))))
+            g.step(T / n, n)
+            U = g.get_state_single()[0]
+            if prec == "learned":
+                fired, dec = g.learned_stats()
+                errs["js_decisions"] = fired / max(dec, 1)
+            g.close()
+            ex = inputs.alfven_wave(N, 1, 1, amp=0.1, t=T)
+            errs[name] = float(np.abs(U[5] - ex.U[5]).mean())
+        errs["vs_js"] = errs["learned"] / errs["js"]
+        errs["vs_weno_z"] = errs["learned"] / errs["weno_z"]
+        out[N] = errs
+    return out
