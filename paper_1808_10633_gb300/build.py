@@ -6,6 +6,9 @@ to this file.  Objects go to _build/ (git-ignored).  The "check" variant
 (libwombat_gb300_check.so, objects in _build_check/) is compiled with
 -DWB_BOUNDS_CHECK=1: the solver kernels test every index they form and
 report a bad one as WB_EINTERNAL instead of touching memory outside an array.
+The "tc" variant (libwombat_gb300_tc.so, objects in _build_tc/) runs the
+learned-weight networks on the 5th-generation tensor cores (tcgen05) instead
+of the per-warp mma.sync form.
 """
 from __future__ import annotations
 
@@ -23,7 +26,9 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwombat_gb300.so")
 VARIANTS = {"release": (OBJ, LIB, []),
             "check": (os.path.join(HERE, "_build_check"), os.path.join(HERE, "libwombat_gb300_check.so"),
-                      ["-DWB_BOUNDS_CHECK=1"])}
+                      ["-DWB_BOUNDS_CHECK=1"]),
+            "tc": (os.path.join(HERE, "_build_tc"), os.path.join(HERE, "libwombat_gb300_tc.so"),
+                   ["-DWB_LEARNED_ENGINE=1"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file extra flags: the FP32 sweep uses fast single-precision division
 # and square root (FP64 code in that file is unaffected)

@@ -46,6 +46,17 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kPartials = 1024;
 
+// Engine of the learned-weight sweep: 0 per warp with mma.sync
+// (wb_sweep_learned.cu, the default: measured 6.3 ms per 256^3 launch), 1 per
+// block on the 5th-generation tensor cores (tcgen05, wb_sweep_learned_tc.cu:
+// 11.9 ms, its three block-wide rounds per field leave the MMA latency
+// exposed); the build's "tc" variant compiles the library with engine 1.
+#ifndef WB_LEARNED_ENGINE
+#define WB_LEARNED_ENGINE 0
+#endif
+
+cudaError_t launch_learned(wb_grid* g, int axis, const wb::SweepArgs<float>& a);
+
 // Optional per-launch CUDA-event timing (wb_step_profiled): an event pair is
 // recorded on the grid's stream around each kernel launch.
 struct Prof {
@@ -87,12 +98,13 @@ struct wb_grid {
     void* er = nullptr;
     void* emf = nullptr;
     uint32_t* d_mlp = nullptr;            // learned weights, fragment order
+    void* d_mlp_tc = nullptr;             // learned weights, tensor-core shared-memory image
     unsigned long long* d_lstats = nullptr;   // detector firings, decisions (learned grids)
     int* d_queue = nullptr;               // per-axis tile counters of the persistent sweeps
     int step_totals = 0;                  // 1: every step also takes the totals of its start state
     cudaStream_t side = nullptr;          // stream the per-step totals run on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    double kappa = 4.0, pjump = 0.5, smooth = 0.0;
+    double kappa = 4.0, pjump = 0.5, smooth = 1.02;   // detector thresholds, smoothness gate
     int tile_policy[3] = {-2, -2, -2};    // build_tiles policy of each axis' table
     int tile_split[3][3] = {};            // per axis: tiles of each shape of a table sorted
                                           // by shape, or all 0 (wb::SweepArgs::split)
@@ -176,8 +188,7 @@ int enqueue_stages(wb_grid* g, Prof* pf) {
             if (rc != WB_OK) return rc;
             if constexpr (sizeof(T) == 4) {
                 if (g->precision == WB_FP32_LEARNED)
-                    WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
-                                                   (float)g->pjump, (float)g->smooth, g->stream));
+                    WB_CK(launch_learned(g, axis, a));
                 else
                     WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
             } else {
@@ -321,10 +332,20 @@ int check_flag(wb_grid* g) {
         WB_CK(cudaStreamSynchronize(g->stream));
         if (f & wb::kFlagBounds)
             return fail(WB_EINTERNAL, "a kernel formed an index outside its array (bounds-checked build)");
+        if (f & wb::kFlagTimeout)
+            return fail(WB_ETIMEOUT, "a learned sweep's wait for the tensor cores ran out");
         return fail(WB_ENONFINITE, "state holds %s",
                     (f & 1u) ? "NaN/Inf values" : "non-positive density or pressure");
     }
     return WB_OK;
+}
+
+cudaError_t launch_learned(wb_grid* g, int axis, const wb::SweepArgs<float>& a) {
+    if (WB_LEARNED_ENGINE == 1)
+        return wb::launch_sweep_learned_tc(axis, a, g->ntiles[axis], g->d_mlp_tc, (float)g->kappa,
+                                           (float)g->pjump, (float)g->smooth, g->stream);
+    return wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa, (float)g->pjump,
+                                    (float)g->smooth, g->stream);
 }
 
 // The address under which the grid's device reads or writes a host array in
@@ -374,7 +395,7 @@ void release(wb_grid* g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
     if (g->side) cudaStreamSynchronize(g->side);
-    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_lstats, g->d_queue,
+    void* ptrs[] = {g->un, g->uk, g->acc, g->flux, g->er, g->emf, g->d_mlp, g->d_mlp_tc, g->d_lstats, g->d_queue,
                     g->d_patches, g->d_links, g->d_tiles[0], g->d_tiles[1], g->d_tiles[2], g->d_blocks,
                     g->d_vblocks, g->d_scalars, g->d_smax, g->d_flag, g->d_partial, g->d_io};
     for (void* p : ptrs)
@@ -411,7 +432,9 @@ std::vector<wb::Tile> build_tiles(const wb_grid* g, int axis, int policy) {
         }
         int ta, tp;
         if (g->precision == WB_FP32_LEARNED) {
-            wb::learned_shape(axis, &ta, &tp);     // the learned sweep's own tile
+            // the learned sweep's own tile
+            if (WB_LEARNED_ENGINE == 1) wb::learned_tc_shape(axis, &ta, &tp);
+            else wb::learned_shape(axis, &ta, &tp);
             best = 0;
         } else {
             wb::sweep_shape(axis, best, &ta, &tp);
@@ -520,8 +543,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     if constexpr (sizeof(T) == 4) {
         if (g->precision == WB_FP32_LEARNED) {
             if (!g->d_mlp) return fail(WB_EINVAL, "learned grid: install the networks with wb_set_mlp first");
-            WB_CK(wb::launch_sweep_learned(axis, a, g->ntiles[axis], g->d_mlp, (float)g->kappa,
-                                           (float)g->pjump, (float)g->smooth, g->stream));
+            WB_CK(launch_learned(g, axis, a));
         } else {
             WB_CK(wb::launch_sweep<T>(axis, a, g->ntiles[axis], g->stream));
         }
@@ -534,7 +556,7 @@ int face_fluxes_impl(wb_grid* g, int axis, double* F_out) {
     WB_CK(cudaMemcpyAsync(F_out, g->d_io, sizeof(double) * 7 * N, cudaMemcpyDeviceToHost,
                           g->stream));
     WB_CK(cudaStreamSynchronize(g->stream));
-    return WB_OK;
+    return check_flag(g);        // a bounds or tensor-core wait failure of the sweep
 }
 
 template <class T>
@@ -726,7 +748,8 @@ int wb_init_grid(const wb_grid_desc* d, const double* U0, const double* b0, void
         return bail(fail(WB_ECUDA, "memset failed"));
     cudaError_t pe = g->precision == WB_FP64 ? wb::prepare_sweep_kernels<double>()
                                              : wb::prepare_sweep_kernels<float>();
-    if (pe == cudaSuccess && g->precision == WB_FP32_LEARNED) pe = wb::prepare_sweep_learned();
+    if (pe == cudaSuccess && g->precision == WB_FP32_LEARNED)
+        pe = WB_LEARNED_ENGINE == 1 ? wb::prepare_sweep_learned_tc() : wb::prepare_sweep_learned();
     if (pe != cudaSuccess) return bail(fail(WB_ECUDA, "kernel attributes: %s", cudaGetErrorString(pe)));
     if ((rc = upload(g, U0, b0)) != WB_OK) return bail(rc);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess)
@@ -1027,6 +1050,14 @@ int wb_set_mlp(wb_grid* g, const float* params, double kappa, double pjump) {
         if (rc != WB_OK) return rc;
     }
     WB_CK(cudaMemcpyAsync(g->d_mlp, frag.data(), sizeof(uint32_t) * words, cudaMemcpyHostToDevice, g->stream));
+    const size_t tcb = wb::mlp_tc_image_bytes();
+    std::vector<unsigned char> img(tcb);
+    wb::mlp_tc_image(params, img.data());
+    if (!g->d_mlp_tc) {
+        int rc = dmalloc(g, &g->d_mlp_tc, tcb);
+        if (rc != WB_OK) return rc;
+    }
+    WB_CK(cudaMemcpyAsync(g->d_mlp_tc, img.data(), tcb, cudaMemcpyHostToDevice, g->stream));
     WB_CK(cudaStreamSynchronize(g->stream));
     g->kappa = kappa;
     g->pjump = pjump;

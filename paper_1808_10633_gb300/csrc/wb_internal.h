@@ -58,6 +58,8 @@ __device__ __forceinline__ long long locate(const PatchDev* __restrict__ patches
 #define WB_BOUNDS_CHECK 0
 #endif
 constexpr unsigned int kFlagBounds = 4u;
+// A bounded wait of a kernel on the tensor cores ran out (WB_ETIMEOUT).
+constexpr unsigned int kFlagTimeout = 8u;
 
 __device__ __forceinline__ long long chk(long long i, long long n, unsigned int* flag) {
 #if WB_BOUNDS_CHECK
@@ -203,6 +205,13 @@ cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles
                                  float kappa, float pjump, float smooth, cudaStream_t s);
 void mlp_fragments(const float* params, uint32_t* out);
 size_t mlp_fragment_words();
+// The learned sweep on the 5th-generation tensor cores (wb_sweep_learned_tc.cu).
+void learned_tc_shape(int axis, int* ta, int* tp);
+cudaError_t prepare_sweep_learned_tc();
+cudaError_t launch_sweep_learned_tc(int axis, const SweepArgs<float>& a, int ntiles, const void* image,
+                                    float kappa, float pjump, float smooth, cudaStream_t s);
+size_t mlp_tc_image_bytes();
+void mlp_tc_image(const float* params, unsigned char* out);
 
 template <class T>
 cudaError_t launch_harvest(const T* src, long long ncells, const PatchDev& P, int axis,

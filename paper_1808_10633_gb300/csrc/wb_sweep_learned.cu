@@ -95,7 +95,7 @@ struct WordsReg {
 };
 
 __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const uint32_t* __restrict__ in,
-                                         float* __restrict__ om, int lane) {
+                                         float* __restrict__ om, int lane, int ntiles = 4) {
     const int g = lane >> 2, t = lane & 3;
 #if WB_LEARNED_HOIST
     const WordsReg W(Ws, lane);
@@ -104,7 +104,7 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
 #endif
     auto Wf = [&](int k) { return __uint_as_float(W(k)); };
 #pragma unroll 1
-    for (int mt = 0; mt < 4; mt++) {
+    for (int mt = 0; mt < ntiles; mt++) {
         const int r0 = 16 * mt + g, r1 = r0 + 8;
         const uint32_t a0 = in[r0 * 4 + t], a1 = in[r1 * 4 + t];
         float c1[4][4];
@@ -271,13 +271,6 @@ struct LearnedWeights {
         float2 x[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) x[k] = __fmul2_rn(dv[k], inv);
-        // one 16-byte store per row (rows 2 lane, 2 lane + 1: the two sides)
-        *reinterpret_cast<uint4*>(in + (2 * lane) * 4) =
-            make_uint4(pack_bf16(x[0].x, x[1].x), pack_bf16(x[2].x, x[3].x), pack_bf16(x[4].x, x[5].x),
-                       pack_bf16(1.0f, 0.0f));
-        *reinterpret_cast<uint4*>(in + (2 * lane + 1) * 4) =
-            make_uint4(pack_bf16(x[0].y, x[1].y), pack_bf16(x[2].y, x[3].y), pack_bf16(x[4].y, x[5].y),
-                       pack_bf16(1.0f, 0.0f));
         bool fire[2];
 #pragma unroll
         for (int side = 0; side < 2; side++) {
@@ -305,12 +298,31 @@ struct LearnedWeights {
             fire[1] = fire[1] || !(mxm + 1e-6f > smooth * (mnm + 1e-6f));
             nfire += (fire[0] ? 1 : 0) + (fire[1] ? 1 : 0);
         }
-        __syncwarp();
-        mlp_warp(W + s * kMlpWords * 32, in, om, lane);
-        __syncwarp();
-        const float4 wl = *reinterpret_cast<const float4*>(om + 4 * lane);
-        __syncwarp();
-        const float2 w0 = make_float2(wl.x, wl.z), w2 = make_float2(wl.y, wl.w);
+        // the network on the rows that use its weights only: the warp's
+        // '+' rows, then its '-' rows, packed to the front of the batch (one
+        // 16-byte store per row), evaluated in as many 16-row tiles as they
+        // fill (rows are independent, so each row's weights are the same)
+        const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
+        const unsigned mp = __ballot_sync(full, !fire[0]), mm = __ballot_sync(full, !fire[1]);
+        const int npl = __popc(mp), nrow = npl + __popc(mm);
+        float2 w0 = splat2(0.0f), w2 = splat2(0.0f);
+        if (nrow > 0) {
+            const int rp = __popc(mp & lt), rm = npl + __popc(mm & lt);
+            if (!fire[0])
+                *reinterpret_cast<uint4*>(in + rp * 4) =
+                    make_uint4(pack_bf16(x[0].x, x[1].x), pack_bf16(x[2].x, x[3].x), pack_bf16(x[4].x, x[5].x),
+                               pack_bf16(1.0f, 0.0f));
+            if (!fire[1])
+                *reinterpret_cast<uint4*>(in + rm * 4) =
+                    make_uint4(pack_bf16(x[0].y, x[1].y), pack_bf16(x[2].y, x[3].y), pack_bf16(x[4].y, x[5].y),
+                               pack_bf16(1.0f, 0.0f));
+            __syncwarp();
+            mlp_warp(W + s * kMlpWords * 32, in, om, lane, (nrow + 15) >> 4);
+            __syncwarp();
+            if (!fire[0]) { w0.x = om[2 * rp]; w2.x = om[2 * rp + 1]; }
+            if (!fire[1]) { w0.y = om[2 * rm]; w2.y = om[2 * rm + 1]; }
+            __syncwarp();
+        }
         const float2 pp = __ffma2_rn(D[1], splat2(-2.0f), __fadd2_rn(D[0], D[2]));
         const float2 qq = __ffma2_rn(D[2], splat2(-2.0f), __fadd2_rn(D[1], D[3]));
         float2 ph = __ffma2_rn(__fmul2_rn(w0, splat2(1.0f / 3.0f)), pp,

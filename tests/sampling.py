@@ -56,7 +56,7 @@ def learned_params_as_run(params):
     return P
 
 
-def oracle_face_flux_learned(st, axis, i, j, k, P, kappa, pjump, margins=None):
+def oracle_face_flux_learned(st, axis, i, j, k, P, kappa, pjump, margins=None, smooth=0.0):
     """Learned-weight eq. FWENO flux through the lower face of cell (i, j, k)
     (library component order), from the FP64 reference network."""
     from oracle import learned as Lr
@@ -69,7 +69,7 @@ def oracle_face_flux_learned(st, axis, i, j, k, P, kappa, pjump, margins=None):
         q = [i, j, k]
         q[axis] = (q[axis] + m - 3) % dims[axis]
         Us[m] = st.U[perm, q[2], q[1], q[0]]
-    Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump, margins)
+    Fh = Lr.interface_flux_learned(Us, st.gamma, P, kappa, pjump, margins, smooth=smooth)
     r = np.empty(7)
     r[0] = Fh[0]
     for gq in range(3):

@@ -120,7 +120,7 @@ def test_fullsize_learned_256_blasts_sampled(orc, wb):
     network trained by the library's own kernels, the bench's detector
     thresholds): sampled interface fluxes against the FP64 reference network
     on the same BF16-rounded weights.  Interfaces whose detector inputs lie
-    within 2 % of a threshold are left out (FP32 and FP64 may decide them
+    within 0.2 % of a threshold are left out (FP32 and FP64 may decide them
     differently); the rest must agree to the BF16 tolerance of the
     random-network parity test."""
     from paper_1808_10633_gb300 import learned as Ln
@@ -131,18 +131,18 @@ def test_fullsize_learned_256_blasts_sampled(orc, wb):
     P = learned_params_as_run(params)
     st = I.add_blasts(I.turbulence(256, seed=1808), seed=1808, nblast=64)
     g = wb.Grid.from_state(st, precision="learned")
-    g.set_mlp(params, 4.0, 0.5)
+    g.set_mlp(params, 4.0, 0.5, smooth=1.02)
     rng = np.random.default_rng(256)
     nx, ny, nz = st.dims
     kept, worst = 0, 0.0
     for axis in range(3):
         F = g.face_fluxes(axis)
-        idx = rng.integers(0, [nx, ny, nz], size=(60, 3))
+        idx = rng.integers(0, [nx, ny, nz], size=(160, 3))
         got, ref = [], []
         for (i, j, k) in idx:
             margins = []
-            r = oracle_face_flux_learned(st, axis, i, j, k, P, 4.0, 0.5, margins)
-            if margins[0] < 2e-2:
+            r = oracle_face_flux_learned(st, axis, i, j, k, P, 4.0, 0.5, margins, smooth=1.02)
+            if margins[0] < 2e-3:
                 continue
             got.append(F[:, (k * ny + j) * nx + i])
             ref.append(r)

@@ -186,7 +186,7 @@ def _sample_learned_fluxes(orc, wb, st, params, kappa, pjump, nsamp, seed, bf16_
     from oracle import learned as Lr
 
     g = wb.Grid.from_state(st, precision="learned")
-    g.set_mlp(params, kappa, pjump, smooth=smooth)
+    g.set_mlp(params, kappa, pjump, smooth=0.0 if smooth is None else smooth)
     rng = np.random.default_rng(seed)
     nx, ny, nz = st.dims
     P = _bf16(params) if bf16_params else np.asarray(params, np.float64)
@@ -257,7 +257,7 @@ def test_learned_sweep_random_network_matches_oracle(orc, wb):
     js = np.concatenate([g.face_fluxes(a)[:, :1] for a in range(3)], axis=1)
     g.close()
     lg = wb.Grid.from_state(st, precision="learned")
-    lg.set_mlp(params, 1e30, 1e30)
+    lg.set_mlp(params, 1e30, 1e30, smooth=0.0)
     ln = np.concatenate([lg.face_fluxes(a)[:, :1] for a in range(3)], axis=1)
     lg.close()
     assert np.abs(ln - js).max() / np.abs(js).max() > 10 * err
@@ -316,27 +316,36 @@ def trained(wb):
     return p
 
 
-def test_learned_gain_on_alfven_wave(orc, wb, trained):
-    """The trained weights recover accuracy where the Jiang-Shu weights lose
-    it (Sec. 2.1: third order near critical points): on the circularly
-    polarised Alfven wave the L1 error against the exact solution is lower
-    than with the Jiang-Shu weights at the same resolution."""
-    errs = {}
-    for mode in ("fp32", "learned"):
-        e = []
-        for N in (16, 32):
-            st = I.alfven_wave(N, 1, 1, amp=0.1)
-            g = wb.Grid.from_state(st, precision=mode)
-            if mode == "learned":
-                g.set_mlp(trained, 4.0, 0.5)
-            T, n = 0.2, int(np.ceil(0.2 / (0.4 / (3 * 1.2 * N))))
-            g.step(T / n, n)
-            U = g.get_state_single()[0]
-            g.close()
-            ex = I.alfven_wave(N, 1, 1, amp=0.1, t=T)
-            e.append(np.abs(U[5] - ex.U[5]).mean())
-        errs[mode] = e
-    assert errs["learned"][-1] < errs["fp32"][-1], errs
+@pytest.fixture(scope="module")
+def trained2(wb):
+    """A second network, trained from other harvested faces and another
+    minibatch stream."""
+    from paper_1808_10633_gb300 import learned as Ln
+
+    rec = Ln.harvest(I.turbulence(64, seed=1808), 20000, seed=11)
+    p, hist = Ln.train(rec, steps=1500, batch=4096, lr=2e-3, lam=1e-3, seed=12)
+    return p
+
+
+def test_learned_gain_on_alfven_wave(wb, trained, trained2):
+    """What the trained networks gain (Sec. 2.1: the Jiang-Shu weights lose
+    accuracy near critical points).  On the circularly polarised Alfven wave
+    the L1 error against the exact solution, with the default smoothness
+    gate, for two independently trained networks: at N = 16 and 32, where
+    the critical points span several cells, at most 1/4 and 2/5 of the
+    Jiang-Shu error (seen: 1/17-1/8 and 1/6); at N = 64, where the
+    Jiang-Shu weights are within the networks' BF16 accuracy of the linear
+    weights and the gate hands back to them, no worse than Jiang-Shu beyond
+    FP32 round-off.  Against WENO-Z (the non-learned remedy Sec. 2.1 names)
+    the networks win at N = 16."""
+    from paper_1808_10633_gb300 import learned as Ln
+
+    for params in (trained, trained2):
+        g = Ln.alfven_gain(params, Ns=(16, 32, 64))
+        assert g[16]["vs_js"] < 0.25 and g[32]["vs_js"] < 0.4, g
+        assert g[64]["vs_js"] < 1.1, g
+        assert g[16]["vs_weno_z"] < 1.0, g
+        assert g[16]["js_decisions"] < 0.95, g          # the networks do act
 
 
 def test_learned_blasts_stay_positive(wb, trained):
@@ -359,7 +368,7 @@ def test_detector_log_counts_every_decision(wb):
     n = 24 ** 3 * 3 * 3 * 14               # interfaces x axes x stages x decisions
     for kappa, pjump, fired in ((1e-30, 1e-30, n), (1e30, 1e30, 0)):
         g = wb.Grid.from_state(st, precision="learned")
-        g.set_mlp(Ln.init_params(seed=2), kappa, pjump)
+        g.set_mlp(Ln.init_params(seed=2), kappa, pjump, smooth=0.0)
         g.step(1e-3, 1)
         assert g.learned_stats(reset=True) == (fired, n)
         assert g.learned_stats() == (0, 0)
