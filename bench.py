@@ -48,8 +48,8 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # benchmark times (profiles/sweep_traffic_fp32_turbulence256.md); reported
 # only at that size and while the sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_N = 256
-SWEEP_TRAFFIC = {"sweep_x": 1188.85e6, "sweep_y": 982.59e6, "sweep_z": 984.48e6}
-SWEEP_TRAFFIC_SOURCES = "fd6f568fa6a1c760"
+SWEEP_TRAFFIC = {"sweep_x": 1177.27e6, "sweep_y": 979.93e6, "sweep_z": 977.63e6}
+SWEEP_TRAFFIC_SOURCES = "17f8f9e1cc313b21"
 
 
 def sweep_sources_hash() -> str:
