@@ -47,6 +47,23 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
         : "r"(a0), "r"(a1), "r"(b0));
 }
 
+// The same with the accumulator input C given apart from D (zeros or the
+// layer's bias), so D needs no initialisation.
+__device__ __forceinline__ void mma_k8_c(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0, float c0, float c1,
+                                         float c2, float c3) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%9,%10};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
+}
+
+__device__ __forceinline__ void mma_k16_c(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1,
+                                          float c0, float c1, float c2, float c3) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%12,%13};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
+}
+
 __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -109,10 +126,7 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
         const uint32_t a0 = in[r0 * 4 + t], a1 = in[r1 * 4 + t];
         float c1[4][4];
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++) {
-            c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
-            mma_k8(c1[nt], a0, a1, W(nt));
-        }
+        for (int nt = 0; nt < 4; nt++) mma_k8_c(c1[nt], a0, a1, W(nt), 0.f, 0.f, 0.f, 0.f);
         uint32_t A2[2][4];
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
@@ -125,10 +139,8 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
             const float blo = Wf(24 + 2 * nt), bhi = Wf(25 + 2 * nt);
-            c2[nt][0] = blo; c2[nt][1] = bhi; c2[nt][2] = blo; c2[nt][3] = bhi;
-#pragma unroll
-            for (int kt = 0; kt < 2; kt++)
-                mma_k16(c2[nt], A2[kt], W(4 + nt * 4 + kt * 2), W(5 + nt * 4 + kt * 2));
+            mma_k16_c(c2[nt], A2[0], W(4 + nt * 4), W(5 + nt * 4), blo, bhi, blo, bhi);
+            mma_k16(c2[nt], A2[1], W(4 + nt * 4 + 2), W(5 + nt * 4 + 2));
         }
         uint32_t A3[2][4];
 #pragma unroll
@@ -139,10 +151,9 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
             A3[kt][3] = gelu_k(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
         }
         const float b3lo = Wf(32), b3hi = Wf(33);
-        float c3[4] = {b3lo, b3hi, b3lo, b3hi};
-#pragma unroll
-        for (int kt = 0; kt < 2; kt++)
-            mma_k16(c3, A3[kt], W(20 + kt * 2), W(21 + kt * 2));
+        float c3[4];
+        mma_k16_c(c3, A3[0], W(20), W(21), b3lo, b3hi, b3lo, b3hi);
+        mma_k16(c3, A3[1], W(22), W(23));
         // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1 (row
         // r0 in c3[0..1], row r1 in c3[2..3]); lane t = 0 takes the softmax
         // of row r0 and lane t = 1 that of row r1
