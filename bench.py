@@ -688,7 +688,7 @@ def main():
     ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--patches", type=int, default=4096,
                     help="patch count of the batched-patch leg (0: skip)")
-    ap.add_argument("--smooth", type=float, default=1.02,
+    ap.add_argument("--smooth", type=float, default=1.03,
                     help="smoothness gate of the learned weights (wb_set_mlp_gate)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="time the FP32 step only (no FP64 leg, L1 comparison, e2e or CPU baseline)")

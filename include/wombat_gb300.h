@@ -375,8 +375,8 @@ int wb_set_mlp(wb_grid *g, const float *params, double kappa, double pjump);
  * Jiang-Shu weights lose accuracy.  Where the stencil is smoother than that
  * the Jiang-Shu weights (within O(dx^2) of the linear weights there) are
  * kept, so that the network's BF16 rounding does not cap the order of the
- * scheme on smooth flow.  Default 1.02 (the indicators of a field differing
- * by more than 2 %); smooth = 0: the networks wherever no detector fires.
+ * scheme on smooth flow.  Default 1.03 (the indicators of a field differing
+ * by more than 3 %); smooth = 0: the networks wherever no detector fires.
  * Errors: WB_EINVAL (not a learned grid, smooth < 0 or not finite). */
 int wb_set_mlp_gate(wb_grid *g, double smooth);
 

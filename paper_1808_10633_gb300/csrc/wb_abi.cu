@@ -104,7 +104,7 @@ struct wb_grid {
     int step_totals = 0;                  // 1: every step also takes the totals of its start state
     cudaStream_t side = nullptr;          // stream the per-step totals run on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    double kappa = 4.0, pjump = 0.5, smooth = 1.02;   // detector thresholds, smoothness gate
+    double kappa = 4.0, pjump = 0.5, smooth = 1.03;   // detector thresholds, smoothness gate
     int tile_policy[3] = {-2, -2, -2};    // build_tiles policy of each axis' table
     int tile_split[3][3] = {};            // per axis: tiles of each shape of a table sorted
                                           // by shape, or all 0 (wb::SweepArgs::split)

@@ -576,6 +576,43 @@ __device__ __forceinline__ void project_all(const Eig<T>& e, const T (&x)[7], T 
     o3[2] = t1 - t2;
 }
 
+// project_all on a (U difference, F difference) pair in packed FP32 lanes:
+// the same coefficients act on both, one instruction for the two.
+#ifndef WB_SWEEP_PAIRPROJ
+#define WB_SWEEP_PAIRPROJ 1            // the difference projection (Jiang-Shu sweeps)
+#endif
+#ifndef WB_SWEEP_PAIRPROJ_NP
+#define WB_SWEEP_PAIRPROJ_NP 0         // the projection of the cells' values (learned sweep)
+#endif
+__device__ __forceinline__ void project_all2(const Eig<float>& e, const float2 (&x)[7], float2 (&o4)[4],
+                                             float2 (&o3)[3]) {
+    const float2 du = __ffma2_rn(splat2(-e.u), x[0], x[1]);
+    const float2 dv1 = __ffma2_rn(splat2(-e.v1), x[0], x[2]);
+    const float2 dv2 = __ffma2_rn(splat2(-e.v2), x[0], x[3]);
+    float2 P = __ffma2_rn(splat2(e.hv2), x[0], x[6]);
+    P = __ffma2_rn(splat2(-e.u), x[1], P);
+    P = __ffma2_rn(splat2(-e.v1), x[2], P);
+    P = __ffma2_rn(splat2(-e.v2), x[3], P);
+    P = __ffma2_rn(splat2(-e.b1), x[4], P);
+    P = __ffma2_rn(splat2(-e.b2), x[5], P);
+    const float2 vpar = __ffma2_rn(splat2(e.be1), dv1, __fmul2_rn(splat2(e.be2), dv2));
+    const float2 bpar = __ffma2_rn(splat2(e.be1), x[4], __fmul2_rn(splat2(e.be2), x[5]));
+    const float2 tf1 = __ffma2_rn(splat2(e.Af), du, __fmul2_rn(splat2(e.Bf), vpar));
+    const float2 tf2 = __ffma2_rn(splat2(e.Cf), bpar, __fmul2_rn(splat2(e.Df), P));
+    const float2 ts1 = __ffma2_rn(splat2(e.As), du, __fmul2_rn(splat2(e.Bs), vpar));
+    const float2 ts2 = __ffma2_rn(splat2(e.Cs), bpar, __fmul2_rn(splat2(e.Ds), P));
+    o4[0] = __ffma2_rn(tf1, splat2(-1.0f), tf2);
+    o4[1] = __ffma2_rn(ts1, splat2(-1.0f), ts2);
+    o4[2] = __fadd2_rn(ts2, ts1);
+    o4[3] = __fadd2_rn(tf2, tf1);
+    const float2 vperp = __ffma2_rn(splat2(e.be1), dv2, __fmul2_rn(splat2(-e.be2), dv1));
+    const float2 bperp = __ffma2_rn(splat2(e.be1), x[5], __fmul2_rn(splat2(-e.be2), x[4]));
+    const float2 t1 = __fmul2_rn(splat2(e.Aa), vperp), t2 = __fmul2_rn(splat2(e.Ba), bperp);
+    o3[0] = __fadd2_rn(t1, t2);
+    o3[1] = __ffma2_rn(splat2(-e.Ee), P, x[0]);
+    o3[2] = __ffma2_rn(t2, splat2(-1.0f), t1);
+}
+
 // single field pair projections (fields processed two at a time keep the
 // projected stencil small): G = 0 fast-/fast+ (s = 0, 6), 1 slow-/slow+
 // (s = 2, 4), 2 Alfven-/Alfven+ (s = 1, 5), 3 entropy (s = 3).
@@ -671,6 +708,31 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         // this thread's shared-memory slots
         T* park = bp + kNBack * bstride;
         T dw[4][5], dg[4][5];
+        if constexpr (sizeof(T) == 4 && WB_SWEEP_PAIRPROJ) {
+            // U and F differences of a stencil step as one packed pair
+            float2 p0[7];
+#pragma unroll
+            for (int f = 0; f < 7; f++) p0[f] = make_float2(sm[(SU + f) * nc + id[0]], sm[(SF + f) * nc + id[0]]);
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                float2 p1[7], x[7], o4[4], o3[3];
+#pragma unroll
+                for (int f = 0; f < 7; f++) {
+                    p1[f] = make_float2(sm[(SU + f) * nc + id[m + 1]], sm[(SF + f) * nc + id[m + 1]]);
+                    x[f] = __ffma2_rn(p0[f], splat2(-1.0f), p1[f]);
+                }
+                project_all2(e, x, o4, o3);
+#pragma unroll
+                for (int f = 0; f < 4; f++) { dw[f][m] = o4[f].x; dg[f][m] = o4[f].y; }
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    park[(f * 5 + m) * bstride] = o3[f].x;
+                    park[((3 + f) * 5 + m) * bstride] = o3[f].y;
+                }
+#pragma unroll
+                for (int f = 0; f < 7; f++) p0[f] = p1[f];
+            }
+        } else {
         T u0[7], f0[7];
         load7(sm, nc, SU, id[0], u0);
         load7(sm, nc, SF, id[0], f0);
@@ -695,6 +757,7 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
             for (int f = 0; f < 3; f++) park[((3 + f) * 5 + m) * bstride] = o3[f];
 #pragma unroll
             for (int f = 0; f < 7; f++) { u0[f] = u1[f]; f0[f] = f1[f]; }
+        }
         }
         // 4-5. fast and slow fields
 #pragma unroll
@@ -759,15 +822,26 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         T w[4][6], g[4][6];
 #pragma unroll
         for (int m = 0; m < 6; m++) {
-            T x[7], o[4];
-            load7(sm, nc, SU, id[m], x);
-            project_fs(e, x, o);
+            if constexpr (sizeof(T) == 4 && WB_SWEEP_PAIRPROJ_NP) {
+                // the cell's U and F as one packed pair (the Alfven/entropy
+                // part of project_all2 is not used and not computed)
+                float2 x[7], o4[4], o3[3];
 #pragma unroll
-            for (int f = 0; f < 4; f++) w[f][m] = o[f];
-            load7(sm, nc, SF, id[m], x);
-            project_fs(e, x, o);
+                for (int f = 0; f < 7; f++) x[f] = make_float2(sm[(SU + f) * nc + id[m]], sm[(SF + f) * nc + id[m]]);
+                project_all2(e, x, o4, o3);
 #pragma unroll
-            for (int f = 0; f < 4; f++) g[f][m] = o[f];
+                for (int f = 0; f < 4; f++) { w[f][m] = o4[f].x; g[f][m] = o4[f].y; }
+            } else {
+                T x[7], o[4];
+                load7(sm, nc, SU, id[m], x);
+                project_fs(e, x, o);
+#pragma unroll
+                for (int f = 0; f < 4; f++) w[f][m] = o[f];
+                load7(sm, nc, SF, id[m], x);
+                project_fs(e, x, o);
+#pragma unroll
+                for (int f = 0; f < 4; f++) g[f][m] = o[f];
+            }
         }
 #pragma unroll
         for (int f = 0; f < 4; f++) {
@@ -780,15 +854,24 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         T w[3][6], g[3][6];
 #pragma unroll
         for (int m = 0; m < 6; m++) {
-            T x[7], o[3];
-            load7(sm, nc, SU, id[m], x);
-            project_ae(e, x, o);
+            if constexpr (sizeof(T) == 4 && WB_SWEEP_PAIRPROJ_NP) {
+                float2 x[7], o4[4], o3[3];
 #pragma unroll
-            for (int f = 0; f < 3; f++) w[f][m] = o[f];
-            load7(sm, nc, SF, id[m], x);
-            project_ae(e, x, o);
+                for (int f = 0; f < 7; f++) x[f] = make_float2(sm[(SU + f) * nc + id[m]], sm[(SF + f) * nc + id[m]]);
+                project_all2(e, x, o4, o3);
 #pragma unroll
-            for (int f = 0; f < 3; f++) g[f][m] = o[f];
+                for (int f = 0; f < 3; f++) { w[f][m] = o3[f].x; g[f][m] = o3[f].y; }
+            } else {
+                T x[7], o[3];
+                load7(sm, nc, SU, id[m], x);
+                project_ae(e, x, o);
+#pragma unroll
+                for (int f = 0; f < 3; f++) w[f][m] = o[f];
+                load7(sm, nc, SF, id[m], x);
+                project_ae(e, x, o);
+#pragma unroll
+                for (int f = 0; f < 3; f++) g[f][m] = o[f];
+            }
         }
 #pragma unroll
         for (int f = 0; f < 3; f++) {
