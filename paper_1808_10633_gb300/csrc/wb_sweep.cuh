@@ -579,10 +579,7 @@ __device__ __forceinline__ void project_all(const Eig<T>& e, const T (&x)[7], T 
 // project_all on a (U difference, F difference) pair in packed FP32 lanes:
 // the same coefficients act on both, one instruction for the two.
 #ifndef WB_SWEEP_PAIRPROJ
-#define WB_SWEEP_PAIRPROJ 1            // the difference projection (Jiang-Shu sweeps)
-#endif
-#ifndef WB_SWEEP_PAIRPROJ_NP
-#define WB_SWEEP_PAIRPROJ_NP 0         // the projection of the cells' values (learned sweep)
+#define WB_SWEEP_PAIRPROJ 1
 #endif
 __device__ __forceinline__ void project_all2(const Eig<float>& e, const float2 (&x)[7], float2 (&o4)[4],
                                              float2 (&o3)[3]) {
@@ -822,26 +819,15 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         T w[4][6], g[4][6];
 #pragma unroll
         for (int m = 0; m < 6; m++) {
-            if constexpr (sizeof(T) == 4 && WB_SWEEP_PAIRPROJ_NP) {
-                // the cell's U and F as one packed pair (the Alfven/entropy
-                // part of project_all2 is not used and not computed)
-                float2 x[7], o4[4], o3[3];
+            T x[7], o[4];
+            load7(sm, nc, SU, id[m], x);
+            project_fs(e, x, o);
 #pragma unroll
-                for (int f = 0; f < 7; f++) x[f] = make_float2(sm[(SU + f) * nc + id[m]], sm[(SF + f) * nc + id[m]]);
-                project_all2(e, x, o4, o3);
+            for (int f = 0; f < 4; f++) w[f][m] = o[f];
+            load7(sm, nc, SF, id[m], x);
+            project_fs(e, x, o);
 #pragma unroll
-                for (int f = 0; f < 4; f++) { w[f][m] = o4[f].x; g[f][m] = o4[f].y; }
-            } else {
-                T x[7], o[4];
-                load7(sm, nc, SU, id[m], x);
-                project_fs(e, x, o);
-#pragma unroll
-                for (int f = 0; f < 4; f++) w[f][m] = o[f];
-                load7(sm, nc, SF, id[m], x);
-                project_fs(e, x, o);
-#pragma unroll
-                for (int f = 0; f < 4; f++) g[f][m] = o[f];
-            }
+            for (int f = 0; f < 4; f++) g[f][m] = o[f];
         }
 #pragma unroll
         for (int f = 0; f < 4; f++) {
@@ -854,24 +840,15 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ sm, int nc,
         T w[3][6], g[3][6];
 #pragma unroll
         for (int m = 0; m < 6; m++) {
-            if constexpr (sizeof(T) == 4 && WB_SWEEP_PAIRPROJ_NP) {
-                float2 x[7], o4[4], o3[3];
+            T x[7], o[3];
+            load7(sm, nc, SU, id[m], x);
+            project_ae(e, x, o);
 #pragma unroll
-                for (int f = 0; f < 7; f++) x[f] = make_float2(sm[(SU + f) * nc + id[m]], sm[(SF + f) * nc + id[m]]);
-                project_all2(e, x, o4, o3);
+            for (int f = 0; f < 3; f++) w[f][m] = o[f];
+            load7(sm, nc, SF, id[m], x);
+            project_ae(e, x, o);
 #pragma unroll
-                for (int f = 0; f < 3; f++) { w[f][m] = o3[f].x; g[f][m] = o3[f].y; }
-            } else {
-                T x[7], o[3];
-                load7(sm, nc, SU, id[m], x);
-                project_ae(e, x, o);
-#pragma unroll
-                for (int f = 0; f < 3; f++) w[f][m] = o[f];
-                load7(sm, nc, SF, id[m], x);
-                project_ae(e, x, o);
-#pragma unroll
-                for (int f = 0; f < 3; f++) g[f][m] = o[f];
-            }
+            for (int f = 0; f < 3; f++) g[f][m] = o[f];
         }
 #pragma unroll
         for (int f = 0; f < 3; f++) {
