@@ -48,8 +48,8 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # benchmark times (profiles/sweep_traffic_fp32_turbulence256.md); reported
 # only at that size and while the sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_N = 256
-SWEEP_TRAFFIC = {"sweep_x": 1177.27e6, "sweep_y": 979.93e6, "sweep_z": 977.63e6}
-SWEEP_TRAFFIC_SOURCES = "17f8f9e1cc313b21"
+SWEEP_TRAFFIC = {"sweep_x": 1184.71e6, "sweep_y": 980.64e6, "sweep_z": 979.13e6}
+SWEEP_TRAFFIC_SOURCES = "3872f467bebff698"
 
 
 def sweep_sources_hash() -> str:
