@@ -173,9 +173,17 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
     }
 }
 
+// The learned sweep projects the stencil's differences like the Jiang-Shu
+// sweep (parked values in shared memory, the weight fragments then read from
+// global memory through L1 instead of a shared copy), or with
+// WB_LEARNED_DELTA=0 the stencil's values in two groups of fields.
+#ifndef WB_LEARNED_DELTA
+#define WB_LEARNED_DELTA 1
+#endif
+
 // Weight policy of the learned scheme.
 struct LearnedWeights {
-    static constexpr bool kDiff = false;     // works on the stencil values themselves
+    static constexpr bool kDiff = WB_LEARNED_DELTA != 0;
     const uint32_t* W;        // shared, [field][34][32]
     uint32_t* in;             // shared, this warp's 64 x 4 words
     float* om;                // shared, this warp's 64 x 2
@@ -266,6 +274,37 @@ struct LearnedWeights {
         float2 D[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) D[k] = __ffma2_rn(V[k], splat2(-1.0f), V[k + 1]);
+        return corr_vd(s, V, D);
+    }
+
+    // The same from the projected differences dw_m = l (U_{m+1} - U_m), dg_m
+    // = l (F_{m+1} - F_m): the split differences are (dg_m +- alpha dw_m)/2,
+    // and the split fluxes are their running sums up to a constant, which
+    // the network's input normalisation (v - mean v) / max|v - mean v|
+    // does not see.
+    __device__ __forceinline__ float corr_d(int s, const float (&dw)[5], const float (&dg)[5], float alpha) {
+        const float ha = 0.5f * alpha;
+        float dP[5], dM[5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            const float hg = 0.5f * dg[m];
+            dP[m] = fmaf(ha, dw[m], hg);
+            dM[m] = fmaf(-ha, dw[m], hg);
+        }
+        float2 D[4], V[6];
+        V[0] = splat2(0.0f);
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            const float2 d = make_float2(dP[k], -dM[4 - k]);
+            if (k < 4) D[k] = d;
+            V[k + 1] = __fadd2_rn(V[k], d);
+        }
+        return corr_vd(s, V, D);
+    }
+
+    // Lane x the '+' side, lane y the '-' side with its stencil reversed:
+    // V the six split fluxes (up to a constant), D their four differences.
+    __device__ __forceinline__ float corr_vd(int s, const float2 (&V)[6], const float2 (&D)[4]) {
         float2 mean = V[0];
 #pragma unroll
         for (int k = 1; k < 6; k++) mean = __fadd2_rn(mean, V[k]);
@@ -358,8 +397,15 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     constexpr int NC = NS * TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
+#if WB_LEARNED_DELTA
+    // weight fragments read from global memory (L1-resident, 30.5 KB); each
+    // thread's back-projection and parked slots after the staged cells
+    const uint32_t* Wsm = mlp;
+    uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNThreadSlots * TA * TP));
+#else
     uint32_t* Wsm = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNBack * TA * TP));
     uint32_t* wbuf = Wsm + kMlpSmemWords;                 // 8 warps x (256 + 128) words
+#endif
 
     const Tile tile = A.tiles[blockIdx.x];
     const PatchDev P = A.patches[tile.x];
@@ -367,7 +413,9 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     const int np = AXIS == 0 ? P.ny : P.nx;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
 
+#if !WB_LEARNED_DELTA
     for (int i = tid; i < kMlpSmemWords; i += TA * TP) Wsm[i] = mlp[i];
+#endif
 
     constexpr int NIT = (NC + TA * TP - 1) / (TA * TP);
     RawCell<T> raw[NIT];
@@ -420,7 +468,7 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
                       pmax > (1.0f + pjump) * pmin, kappa, smooth};
     T F[7];
     T* bp = sm + kNSlot * NC + tid;
-    interface_flux<T>(sm, NC, id, T(A.gamma), bp, TA * TP, lw, F);
+    interface_flux<T, LearnedWeights, WB_LEARNED_DELTA != 0>(sm, NC, id, T(A.gamma), bp, TA * TP, lw, F);
     if (A.lstats) {
         // detector statistics: firings and decisions (7 fields x 2 sides) of
         // the valid interfaces, one pair of atomics per warp
@@ -455,7 +503,12 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
 
 template <int AXIS>
 constexpr size_t learned_smem_bytes() {
+#if WB_LEARNED_DELTA
+    return sizeof(float) * ((size_t)kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP
+                            + (size_t)kNThreadSlots * Shape<AXIS>::TA * Shape<AXIS>::TP) + sizeof(uint32_t) * 8 * 384;
+#else
     return smem_bytes<float, AXIS>() + sizeof(uint32_t) * (kMlpSmemWords + 8 * 384);
+#endif
 }
 
 }  // namespace
