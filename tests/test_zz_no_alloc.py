@@ -59,3 +59,57 @@ def test_noalloc_rejects_sizes_beyond_the_maximum(wb):
         wb.conserved_totals_noalloc(buf.data_ptr(), "fp64", (1 << 34) + 1, 1.0, buf.data_ptr())
     assert e.value.code == wb.WB_EINVAL
     assert "WB_NOALLOC_MAX_CELLS" in str(e.value)
+
+
+RESET_SCRIPT = r"""
+import ctypes, os, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1808_10633_gb300 import wombat as wb
+wb.load()
+# the CUDA runtime the library loaded (the same instance, not a second copy)
+path = next(l.split()[-1] for l in open("/proc/self/maps") if "libcudart" in l)
+rt = ctypes.CDLL(path)
+vp = ctypes.c_void_p
+rt.cudaMalloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
+rt.cudaMemcpy.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+rt.cudaFree.argtypes = [vp]
+rng = np.random.default_rng(7)
+n, dV = 100003, 0.25
+for round_ in range(2):
+    state = rng.standard_normal(8 * n)
+    ds, do = vp(), vp()
+    assert rt.cudaMalloc(ctypes.byref(ds), state.nbytes) == 0
+    assert rt.cudaMalloc(ctypes.byref(do), 64) == 0
+    assert rt.cudaMemcpy(ds, state.ctypes.data, state.nbytes, 1) == 0
+    wb.conserved_totals_noalloc(ds.value, "fp64", n, dV, do.value)
+    assert rt.cudaDeviceSynchronize() == 0
+    out = np.empty(8)
+    assert rt.cudaMemcpy(out.ctypes.data, do, 64, 2) == 0
+    # state layout rho, mx, my, mz, E, bx, by, bz; totals (rho, m, B, E)
+    order = [0, 1, 2, 3, 5, 6, 7, 4]
+    ref = state.reshape(8, n).sum(axis=1)[order] * dV
+    scale = np.abs(state).reshape(8, n).sum(axis=1)[order] * dV
+    assert np.all(np.abs(out - ref) <= 1e-13 * scale), (round_, out, ref)
+    rt.cudaFree(ds)
+    rt.cudaFree(do)
+    if round_ == 0:
+        assert rt.cudaDeviceReset() == 0      # ends this process's context only
+print("noalloc after reset OK")
+"""
+
+
+def test_noalloc_after_device_reset(wb):
+    """A caller (or another library in its process) may reset the device
+    between calls: the module is loaded again and the scratch array may move.
+    Each call outside stream capture looks its address up again, so the sums
+    stay right.  Run in a process of its own (the reset would also end the
+    context torch holds in this one)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", RESET_SCRIPT, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "noalloc after reset OK" in r.stdout
