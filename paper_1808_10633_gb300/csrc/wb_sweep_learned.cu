@@ -26,9 +26,21 @@
 namespace wb {
 namespace {
 
-#ifndef WB_LEARNED_MINB
-#define WB_LEARNED_MINB 2                        // resident 256-thread blocks per SM (128 registers)
+#ifndef WB_LEARNED_NT
+#define WB_LEARNED_NT 256                        // threads (interfaces) per tile
 #endif
+#ifndef WB_LEARNED_MINB
+#define WB_LEARNED_MINB 2                        // resident blocks per SM (256 threads: 128 registers)
+#endif
+constexpr int kLearnedNT = WB_LEARNED_NT;
+static_assert(kLearnedNT % 32 == 0 && kLearnedNT >= 64 && kLearnedNT <= 512, "learned tile size");
+// Tile of the learned sweep: the Jiang-Shu sweep's extent along the axis,
+// kLearnedNT / TA pencils.
+template <int AXIS>
+struct LShape {
+    static constexpr int TA = Shape<AXIS>::TA, TP = kLearnedNT / TA;
+    static_assert(TA * TP == kLearnedNT, "learned tile size must be a multiple of the tile's axis extent");
+};
 
 constexpr int kMlpWords = 34;                    // per lane per field
 constexpr float kGeluK = 0.851f;                 // gelu(x) = x/2 (1 + tanh(kGeluK x))
@@ -111,58 +123,80 @@ struct WordsReg {
     __device__ __forceinline__ uint32_t operator()(int k) const { return w[k]; }
 };
 
-__device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const uint32_t* __restrict__ in,
-                                         float* __restrict__ om, int lane, int ntiles = 4) {
+// K row tiles of 16 starting at tile mt0, their products interleaved (K
+// independent chains of MMAs, GELUs and softmaxes for the scheduler).
+template <int K, class Words>
+__device__ __forceinline__ void mlp_tiles(const Words& W, const uint32_t* __restrict__ in, float* __restrict__ om,
+                                          int lane, int mt0) {
     const int g = lane >> 2, t = lane & 3;
-#if WB_LEARNED_HOIST
-    const WordsReg W(Ws, lane);
-#else
-    const WordsSmem W{Ws, lane};
-#endif
     auto Wf = [&](int k) { return __uint_as_float(W(k)); };
-#pragma unroll 1
-    for (int mt = 0; mt < ntiles; mt++) {
-        const int r0 = 16 * mt + g, r1 = r0 + 8;
-        const uint32_t a0 = in[r0 * 4 + t], a1 = in[r1 * 4 + t];
-        float c1[4][4];
+    uint32_t a0[K], a1[K];
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++) mma_k8_c(c1[nt], a0, a1, W(nt), 0.f, 0.f, 0.f, 0.f);
-        uint32_t A2[2][4];
+    for (int q = 0; q < K; q++) {
+        const int r0 = 16 * (mt0 + q) + g;
+        a0[q] = in[r0 * 4 + t];
+        a1[q] = in[(r0 + 8) * 4 + t];
+    }
+    float c1[K][4][4];
 #pragma unroll
-        for (int kt = 0; kt < 2; kt++) {
-            A2[kt][0] = gelu_k(c1[2 * kt][0], c1[2 * kt][1]);
-            A2[kt][1] = gelu_k(c1[2 * kt][2], c1[2 * kt][3]);
-            A2[kt][2] = gelu_k(c1[2 * kt + 1][0], c1[2 * kt + 1][1]);
-            A2[kt][3] = gelu_k(c1[2 * kt + 1][2], c1[2 * kt + 1][3]);
-        }
-        float c2[4][4];
+    for (int nt = 0; nt < 4; nt++) {
+        const uint32_t b = W(nt);
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++) {
-            const float blo = Wf(24 + 2 * nt), bhi = Wf(25 + 2 * nt);
-            mma_k16_c(c2[nt], A2[0], W(4 + nt * 4), W(5 + nt * 4), blo, bhi, blo, bhi);
-            mma_k16(c2[nt], A2[1], W(4 + nt * 4 + 2), W(5 + nt * 4 + 2));
-        }
-        uint32_t A3[2][4];
+        for (int q = 0; q < K; q++) mma_k8_c(c1[q][nt], a0[q], a1[q], b, 0.f, 0.f, 0.f, 0.f);
+    }
+    uint32_t A2[K][2][4];
+#pragma unroll
+    for (int q = 0; q < K; q++)
 #pragma unroll
         for (int kt = 0; kt < 2; kt++) {
-            A3[kt][0] = gelu_k(c2[2 * kt][0], c2[2 * kt][1]);
-            A3[kt][1] = gelu_k(c2[2 * kt][2], c2[2 * kt][3]);
-            A3[kt][2] = gelu_k(c2[2 * kt + 1][0], c2[2 * kt + 1][1]);
-            A3[kt][3] = gelu_k(c2[2 * kt + 1][2], c2[2 * kt + 1][3]);
+            A2[q][kt][0] = gelu_k(c1[q][2 * kt][0], c1[q][2 * kt][1]);
+            A2[q][kt][1] = gelu_k(c1[q][2 * kt][2], c1[q][2 * kt][3]);
+            A2[q][kt][2] = gelu_k(c1[q][2 * kt + 1][0], c1[q][2 * kt + 1][1]);
+            A2[q][kt][3] = gelu_k(c1[q][2 * kt + 1][2], c1[q][2 * kt + 1][3]);
         }
-        const float b3lo = Wf(32), b3hi = Wf(33);
-        float c3[4];
-        mma_k16_c(c3, A3[0], W(20), W(21), b3lo, b3hi, b3lo, b3hi);
-        mma_k16(c3, A3[1], W(22), W(23));
+    float c2[K][4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; nt++) {
+        const float blo = Wf(24 + 2 * nt), bhi = Wf(25 + 2 * nt);
+        const uint32_t b0 = W(4 + nt * 4), b1 = W(5 + nt * 4), b2 = W(6 + nt * 4), b3 = W(7 + nt * 4);
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            mma_k16_c(c2[q][nt], A2[q][0], b0, b1, blo, bhi, blo, bhi);
+            mma_k16(c2[q][nt], A2[q][1], b2, b3);
+        }
+    }
+    uint32_t A3[K][2][4];
+#pragma unroll
+    for (int q = 0; q < K; q++)
+#pragma unroll
+        for (int kt = 0; kt < 2; kt++) {
+            A3[q][kt][0] = gelu_k(c2[q][2 * kt][0], c2[q][2 * kt][1]);
+            A3[q][kt][1] = gelu_k(c2[q][2 * kt][2], c2[q][2 * kt][3]);
+            A3[q][kt][2] = gelu_k(c2[q][2 * kt + 1][0], c2[q][2 * kt + 1][1]);
+            A3[q][kt][3] = gelu_k(c2[q][2 * kt + 1][2], c2[q][2 * kt + 1][3]);
+        }
+    const float b3lo = Wf(32), b3hi = Wf(33);
+    float c3[K][4];
+    {
+        const uint32_t b0 = W(20), b1 = W(21), b2 = W(22), b3 = W(23);
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            mma_k16_c(c3[q], A3[q][0], b0, b1, b3lo, b3hi, b3lo, b3hi);
+            mma_k16(c3[q], A3[q][1], b2, b3);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const int r0 = 16 * (mt0 + q) + g, r1 = r0 + 8;
         // logits z0, z1 sit in lane t = 0 of each quad, z2 in lane t = 1 (row
         // r0 in c3[0..1], row r1 in c3[2..3]); lane t = 0 takes the softmax
         // of row r0 and lane t = 1 that of row r1
-        const float z2a = __shfl_down_sync(0xffffffffu, c3[0], 1);
-        const float z0b = __shfl_up_sync(0xffffffffu, c3[2], 1);
-        const float z1b = __shfl_up_sync(0xffffffffu, c3[3], 1);
+        const float z2a = __shfl_down_sync(0xffffffffu, c3[q][0], 1);
+        const float z0b = __shfl_up_sync(0xffffffffu, c3[q][2], 1);
+        const float z1b = __shfl_up_sync(0xffffffffu, c3[q][3], 1);
         if (t < 2) {
-            const float z0 = t == 0 ? c3[0] : z0b, z1 = t == 0 ? c3[1] : z1b;
-            const float z2 = t == 0 ? z2a : c3[2];
+            const float z0 = t == 0 ? c3[q][0] : z0b, z1 = t == 0 ? c3[q][1] : z1b;
+            const float z2 = t == 0 ? z2a : c3[q][2];
             const float zm = fmaxf(z0, fmaxf(z1, z2));
             const float e0 = __expf(z0 - zm), e1 = __expf(z1 - zm), e2 = __expf(z2 - zm);
             const float inv = __fdividef(1.0f, e0 + e1 + e2);
@@ -171,6 +205,26 @@ __device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const 
             om[2 * r + 1] = e2 * inv;
         }
     }
+}
+
+// Row tiles evaluated together by one warp (1: one tile at a time).
+#ifndef WB_LEARNED_ILP
+#define WB_LEARNED_ILP 1
+#endif
+__device__ __forceinline__ void mlp_warp(const uint32_t* __restrict__ Ws, const uint32_t* __restrict__ in,
+                                         float* __restrict__ om, int lane, int ntiles = 4) {
+#if WB_LEARNED_HOIST
+    const WordsReg W(Ws, lane);
+#else
+    const WordsSmem W{Ws, lane};
+#endif
+    int mt = 0;
+#if WB_LEARNED_ILP > 1
+#pragma unroll 1
+    for (; mt + 2 <= ntiles; mt += 2) mlp_tiles<2>(W, in, om, lane, mt);
+#endif
+#pragma unroll 1
+    for (; mt < ntiles; mt++) mlp_tiles<1>(W, in, om, lane, mt);
 }
 
 // The learned sweep projects the stencil's differences like the Jiang-Shu
@@ -388,11 +442,11 @@ struct LearnedWeights {
 };
 
 template <int AXIS>
-__global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(const SweepArgs<float> A,
+__global__ void __launch_bounds__(kLearnedNT, WB_LEARNED_MINB) sweep_learned_kernel(const SweepArgs<float> A,
                                                                const uint32_t* __restrict__ mlp,
                                                                float kappa, float pjump, float smooth) {
     using T = float;
-    constexpr int TA = Shape<AXIS>::TA, TP = Shape<AXIS>::TP;
+    constexpr int TA = LShape<AXIS>::TA, TP = LShape<AXIS>::TP;
     constexpr int NS = TA + 5;
     constexpr int NC = NS * TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -404,7 +458,7 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
     uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNThreadSlots * TA * TP));
 #else
     uint32_t* Wsm = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNBack * TA * TP));
-    uint32_t* wbuf = Wsm + kMlpSmemWords;                 // 8 warps x (256 + 128) words
+    uint32_t* wbuf = Wsm + kMlpSmemWords;                 // per warp 256 + 128 words
 #endif
 
     const Tile tile = A.tiles[blockIdx.x];
@@ -503,19 +557,20 @@ __global__ void __launch_bounds__(256, WB_LEARNED_MINB) sweep_learned_kernel(con
 
 template <int AXIS>
 constexpr size_t learned_smem_bytes() {
+    constexpr size_t TA = LShape<AXIS>::TA, TP = LShape<AXIS>::TP;
+    constexpr size_t wbuf = sizeof(uint32_t) * (kLearnedNT / 32) * 384;     // per warp 256 + 128 words
 #if WB_LEARNED_DELTA
-    return sizeof(float) * ((size_t)kNSlot * (Shape<AXIS>::TA + 5) * Shape<AXIS>::TP
-                            + (size_t)kNThreadSlots * Shape<AXIS>::TA * Shape<AXIS>::TP) + sizeof(uint32_t) * 8 * 384;
+    return sizeof(float) * (kNSlot * (TA + 5) * TP + kNThreadSlots * TA * TP) + wbuf;
 #else
-    return smem_bytes<float, AXIS>() + sizeof(uint32_t) * (kMlpSmemWords + 8 * 384);
+    return sizeof(float) * (kNSlot * (TA + 5) * TP + kNBack * TA * TP) + sizeof(uint32_t) * kMlpSmemWords + wbuf;
 #endif
 }
 
 }  // namespace
 
 void learned_shape(int axis, int* ta, int* tp) {
-    *ta = axis == 0 ? Shape<0>::TA : Shape<1>::TA;
-    *tp = axis == 0 ? Shape<0>::TP : Shape<1>::TP;
+    *ta = axis == 0 ? LShape<0>::TA : LShape<1>::TA;
+    *tp = axis == 0 ? LShape<0>::TP : LShape<1>::TP;
 }
 
 cudaError_t prepare_sweep_learned() {
@@ -534,13 +589,13 @@ cudaError_t launch_sweep_learned(int axis, const SweepArgs<float>& a, int ntiles
                                  float kappa, float pjump, float smooth, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (axis == 0)
-        sweep_learned_kernel<0><<<ntiles, dim3(Shape<0>::TA, Shape<0>::TP), learned_smem_bytes<0>(), s>>>(
+        sweep_learned_kernel<0><<<ntiles, dim3(LShape<0>::TA, LShape<0>::TP), learned_smem_bytes<0>(), s>>>(
             a, mlp, kappa, pjump, smooth);
     else if (axis == 1)
-        sweep_learned_kernel<1><<<ntiles, dim3(Shape<1>::TP, Shape<1>::TA), learned_smem_bytes<1>(), s>>>(
+        sweep_learned_kernel<1><<<ntiles, dim3(LShape<1>::TP, LShape<1>::TA), learned_smem_bytes<1>(), s>>>(
             a, mlp, kappa, pjump, smooth);
     else
-        sweep_learned_kernel<2><<<ntiles, dim3(Shape<2>::TP, Shape<2>::TA), learned_smem_bytes<2>(), s>>>(
+        sweep_learned_kernel<2><<<ntiles, dim3(LShape<2>::TP, LShape<2>::TA), learned_smem_bytes<2>(), s>>>(
             a, mlp, kappa, pjump, smooth);
     return cudaGetLastError();
 }
