@@ -66,15 +66,17 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 // Sec. 2.1: phi_N(a,b,c,d) = 1/3 w0 (a-2b+c) + 1/6 (w2-1/2)(b-2c+d) with
 // IS_0..2 as printed, alpha_k = d_k/(eps+IS_k)^2, d = (1, 6, 3), eps = 1e-6.
+// The weights depend only on the ratios of the eps + IS_k, so each is formed
+// divided by three, (13/3) t^2 + t'^2 + eps/3: one multiply and two fused
+// multiply-adds, the eps folded in.
 __device__ __forceinline__ double phi_n(double a, double b, double c, double d) {
-    const double eps = 1e-6;
-    double t0 = a - b, t1 = a - 3.0 * b;
-    double is0 = 13.0 * t0 * t0 + 3.0 * t1 * t1;
-    double t2 = b - c, t3 = b + c;
-    double is1 = 13.0 * t2 * t2 + 3.0 * t3 * t3;
-    double t4 = c - d, t5 = 3.0 * c - d;
-    double is2 = 13.0 * t4 * t4 + 3.0 * t5 * t5;
-    double e0 = eps + is0, e1 = eps + is1, e2 = eps + is2;
+    const double eps3 = 1e-6 / 3.0, k13 = 13.0 / 3.0;
+    const double t0 = a - b, t1 = a - 3.0 * b;
+    const double t2 = b - c, t3 = b + c;
+    const double t4 = c - d, t5 = 3.0 * c - d;
+    double e0 = fma(k13 * t0, t0, fma(t1, t1, eps3));
+    double e1 = fma(k13 * t2, t2, fma(t3, t3, eps3));
+    double e2 = fma(k13 * t4, t4, fma(t5, t5, eps3));
     e0 *= e0; e1 *= e1; e2 *= e2;
     // omega_k = (d_k / e_k) / sum_j (d_j / e_j): one division in FP64
     double n0 = e1 * e2, n2 = 3.0 * e0 * e1;
@@ -84,14 +86,13 @@ __device__ __forceinline__ double phi_n(double a, double b, double c, double d) 
 }
 
 __device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
-    const float eps = 1e-6f;
-    float t0 = a - b, t1 = a - 3.0f * b;
-    float is0 = 13.0f * t0 * t0 + 3.0f * t1 * t1;
-    float t2 = b - c, t3 = b + c;
-    float is1 = 13.0f * t2 * t2 + 3.0f * t3 * t3;
-    float t4 = c - d, t5 = 3.0f * c - d;
-    float is2 = 13.0f * t4 * t4 + 3.0f * t5 * t5;
-    float e0 = eps + is0, e1 = eps + is1, e2 = eps + is2;
+    const float eps3 = 1e-6f / 3.0f, k13 = 13.0f / 3.0f;
+    const float t0 = a - b, t1 = a - 3.0f * b;
+    const float t2 = b - c, t3 = b + c;
+    const float t4 = c - d, t5 = 3.0f * c - d;
+    const float e0 = fmaf(k13 * t0, t0, fmaf(t1, t1, eps3));
+    const float e1 = fmaf(k13 * t2, t2, fmaf(t3, t3, eps3));
+    const float e2 = fmaf(k13 * t4, t4, fmaf(t5, t5, eps3));
     // reciprocals keep the FP32 range: (eps+IS)^2 products could overflow
     float a0 = 1.0f / (e0 * e0), a1 = 6.0f / (e1 * e1), a2 = 3.0f / (e2 * e2);
     float r = 1.0f / (a0 + a1 + a2);
@@ -108,13 +109,15 @@ __device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
 #endif
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 phi_n2(float2 a, float2 b, float2 c, float2 d) {
+    // (eps + IS_k) / 3 as in phi_n
+    const float2 k13 = splat2(13.0f / 3.0f), eps3 = splat2(1e-6f / 3.0f);
     const float2 t0 = __ffma2_rn(b, splat2(-1.0f), a), t1 = __ffma2_rn(b, splat2(-3.0f), a);
-    const float2 is0 = __ffma2_rn(__fmul2_rn(t0, splat2(13.0f)), t0, __fmul2_rn(__fmul2_rn(t1, splat2(3.0f)), t1));
     const float2 t2 = __ffma2_rn(c, splat2(-1.0f), b), t3 = __fadd2_rn(b, c);
-    const float2 is1 = __ffma2_rn(__fmul2_rn(t2, splat2(13.0f)), t2, __fmul2_rn(__fmul2_rn(t3, splat2(3.0f)), t3));
-    const float2 t4 = __ffma2_rn(d, splat2(-1.0f), c), t5 = __ffma2_rn(c, splat2(3.0f), __fmul2_rn(d, splat2(-1.0f)));
-    const float2 is2 = __ffma2_rn(__fmul2_rn(t4, splat2(13.0f)), t4, __fmul2_rn(__fmul2_rn(t5, splat2(3.0f)), t5));
-    float2 e0 = __fadd2_rn(is0, splat2(1e-6f)), e1 = __fadd2_rn(is1, splat2(1e-6f)), e2 = __fadd2_rn(is2, splat2(1e-6f));
+    // t5 enters squared: d - 3c serves for 3c - d
+    const float2 t4 = __ffma2_rn(d, splat2(-1.0f), c), t5 = __ffma2_rn(c, splat2(-3.0f), d);
+    float2 e0 = __ffma2_rn(__fmul2_rn(t0, k13), t0, __ffma2_rn(t1, t1, eps3));
+    float2 e1 = __ffma2_rn(__fmul2_rn(t2, k13), t2, __ffma2_rn(t3, t3, eps3));
+    float2 e2 = __ffma2_rn(__fmul2_rn(t4, k13), t4, __ffma2_rn(t5, t5, eps3));
     e0 = __fmul2_rn(e0, e0);
     e1 = __fmul2_rn(e1, e1);
     e2 = __fmul2_rn(e2, e2);
