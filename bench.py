@@ -39,9 +39,10 @@ UNIT = "zone-updates/s"
 # formulas (add/sub/mul = 1, FMA = 2, div/sqrt = 1): eigen-structure 100,
 # interface average 16, central flux 35, differences of the stencil 70,
 # their projection 10 x 68, split differences and two phi_N per field
-# 7 x 119 (the eps of each smoothness indicator folded into its fused
-# multiply-adds), back-projection 80.
-SWEEP_FLOPS_PER_INTERFACE = 1814
+# 7 x 114 (the eps of each smoothness indicator folded into its fused
+# multiply-adds, phi_N taken on twice the split differences and halved
+# once), back-projection 80.
+SWEEP_FLOPS_PER_INTERFACE = 1779
 SWEEP_FLOPS_PER_STAGED_CELL = 80
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the

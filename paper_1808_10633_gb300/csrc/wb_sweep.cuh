@@ -69,8 +69,10 @@ __device__ __forceinline__ int wrap(int v, int n) {
 // The weights depend only on the ratios of the eps + IS_k, so each is formed
 // divided by three, (13/3) t^2 + t'^2 + eps/3: one multiply and two fused
 // multiply-adds, the eps folded in.
-__device__ __forceinline__ double phi_n(double a, double b, double c, double d) {
-    const double eps3 = 1e-6 / 3.0, k13 = 13.0 / 3.0;
+// eps3 = eps / 3; phi_N(s a, s b, s c, s d) with s^2 eps3 is s phi_N(a, b, c, d).
+constexpr double kEps3 = 1e-6 / 3.0;
+__device__ __forceinline__ double phi_n(double a, double b, double c, double d, double eps3 = kEps3) {
+    const double k13 = 13.0 / 3.0;
     const double t0 = a - b, t1 = a - 3.0 * b;
     const double t2 = b - c, t3 = b + c;
     const double t4 = c - d, t5 = 3.0 * c - d;
@@ -85,8 +87,9 @@ __device__ __forceinline__ double phi_n(double a, double b, double c, double d) 
     return w0 * (a - 2.0 * b + c) * (1.0 / 3.0) + (w2 - 0.5) * (b - 2.0 * c + d) * (1.0 / 6.0);
 }
 
-__device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
-    const float eps3 = 1e-6f / 3.0f, k13 = 13.0f / 3.0f;
+constexpr float kEps3f = 1e-6f / 3.0f;
+__device__ __forceinline__ float phi_n(float a, float b, float c, float d, float eps3 = kEps3f) {
+    const float k13 = 13.0f / 3.0f;
     const float t0 = a - b, t1 = a - 3.0f * b;
     const float t2 = b - c, t3 = b + c;
     const float t4 = c - d, t5 = 3.0f * c - d;
@@ -108,9 +111,9 @@ __device__ __forceinline__ float phi_n(float a, float b, float c, float d) {
 #define WB_SWEEP_PACKED 1
 #endif
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 phi_n2(float2 a, float2 b, float2 c, float2 d) {
+__device__ __forceinline__ float2 phi_n2(float2 a, float2 b, float2 c, float2 d, float eps3f = kEps3f) {
     // (eps + IS_k) / 3 as in phi_n
-    const float2 k13 = splat2(13.0f / 3.0f), eps3 = splat2(1e-6f / 3.0f);
+    const float2 k13 = splat2(13.0f / 3.0f), eps3 = splat2(eps3f);
     const float2 t0 = __ffma2_rn(b, splat2(-1.0f), a), t1 = __ffma2_rn(b, splat2(-3.0f), a);
     const float2 t2 = __ffma2_rn(c, splat2(-1.0f), b), t3 = __fadd2_rn(b, c);
     // t5 enters squared: d - 3c serves for 3c - d
@@ -210,26 +213,41 @@ __device__ __forceinline__ T weno_corr(const T (&w)[6], const T (&g)[6], T alpha
 // The same correction from the projected differences of the stencil,
 // dw_m = l_s (U_{m+1} - U_m), dg_m = l_s (F_{m+1} - F_m), m = 0..4 (the
 // projection is linear, so D+-_{m+1/2} = (dg_m +- alpha dw_m) / 2).
+template <class T> constexpr T eps3_of() { return sizeof(T) == 4 ? T(kEps3f) : T(kEps3); }
 template <class T, bool Z = false>
 __device__ __forceinline__ T weno_corr_d(const T (&dw)[5], const T (&dg)[5], T alpha) {
-    const T ha = T(0.5) * alpha;
-    T hg[5];
-#pragma unroll
-    for (int m = 0; m < 5; m++) hg[m] = T(0.5) * dg[m];
-    const T dp0 = hg[0] + ha * dw[0], dp1 = hg[1] + ha * dw[1], dp2 = hg[2] + ha * dw[2], dp3 = hg[3] + ha * dw[3];
-    const T dm1 = hg[1] - ha * dw[1], dm2 = hg[2] - ha * dw[2], dm3 = hg[3] - ha * dw[3], dm4 = hg[4] - ha * dw[4];
-    if constexpr (Z && WB_SWEEP_PACKED && sizeof(T) == 4) {
-        const float2 ph = phi_n_z2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
-                                   make_float2(dm1, dp3));
-        return ph.x - ph.y;
-    } else if constexpr (Z) {
-        return phi_n_z(dm4, dm3, dm2, dm1) - phi_n_z(dp0, dp1, dp2, dp3);
-    } else if constexpr (WB_SWEEP_PACKED && sizeof(T) == 4) {
-        const float2 ph = phi_n2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
-                                 make_float2(dm1, dp3));
-        return ph.x - ph.y;
+    if constexpr (!Z) {
+        // phi_N taken on 2 D+- = dg_m +- alpha dw_m with 4 eps and halved:
+        // scaling by two is exact, so the value is the same, and the halving
+        // of the eight differences becomes one multiply
+        const T dp0 = dg[0] + alpha * dw[0], dp1 = dg[1] + alpha * dw[1], dp2 = dg[2] + alpha * dw[2],
+                dp3 = dg[3] + alpha * dw[3];
+        const T dm1 = dg[1] - alpha * dw[1], dm2 = dg[2] - alpha * dw[2], dm3 = dg[3] - alpha * dw[3],
+                dm4 = dg[4] - alpha * dw[4];
+        constexpr T eps3 = T(4) * eps3_of<T>();
+        if constexpr (WB_SWEEP_PACKED && sizeof(T) == 4) {
+            const float2 ph = phi_n2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
+                                     make_float2(dm1, dp3), eps3);
+            return T(0.5) * (ph.x - ph.y);
+        } else {
+            return T(0.5) * (phi_n(dm4, dm3, dm2, dm1, eps3) - phi_n(dp0, dp1, dp2, dp3, eps3));
+        }
     } else {
-        return phi_n(dm4, dm3, dm2, dm1) - phi_n(dp0, dp1, dp2, dp3);
+        const T ha = T(0.5) * alpha;
+        T hg[5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) hg[m] = T(0.5) * dg[m];
+        const T dp0 = hg[0] + ha * dw[0], dp1 = hg[1] + ha * dw[1], dp2 = hg[2] + ha * dw[2],
+                dp3 = hg[3] + ha * dw[3];
+        const T dm1 = hg[1] - ha * dw[1], dm2 = hg[2] - ha * dw[2], dm3 = hg[3] - ha * dw[3],
+                dm4 = hg[4] - ha * dw[4];
+        if constexpr (WB_SWEEP_PACKED && sizeof(T) == 4) {
+            const float2 ph = phi_n_z2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
+                                       make_float2(dm1, dp3));
+            return ph.x - ph.y;
+        } else {
+            return phi_n_z(dm4, dm3, dm2, dm1) - phi_n_z(dp0, dp1, dp2, dp3);
+        }
     }
 }
 
