@@ -42,7 +42,11 @@ struct LShape {
     static_assert(TA * TP == kLearnedNT, "learned tile size must be a multiple of the tile's axis extent");
 };
 
-constexpr int kMlpWords = 34;                    // per lane per field
+constexpr int kMlpWords = 36;                    // per lane per field (34 used), 9 groups of 4
+// Word k of lane `lane` within one field's fragment table: groups of four
+// consecutive words per lane, the 32 lanes' groups side by side, so that a
+// warp reads one group of every lane as one coalesced 16-byte load each.
+__host__ __device__ constexpr int frag_index(int k, int lane) { return ((k >> 2) * 32 + lane) * 4 + (k & 3); }
 constexpr float kGeluK = 0.851f;                 // gelu(x) = x/2 (1 + tanh(kGeluK x))
 constexpr int kMlpSmemWords = WB_MLP_NFIELD * kMlpWords * 32;
 
@@ -112,15 +116,19 @@ __device__ __forceinline__ uint32_t gelu_k(float a, float b) {
 struct WordsSmem {
     const uint32_t* W;
     int lane;
-    __device__ __forceinline__ uint32_t operator()(int k) const { return W[k * 32 + lane]; }
+    __device__ __forceinline__ uint32_t operator()(int k) const { return W[frag_index(k, lane)]; }
+    __device__ __forceinline__ uint4 q(int grp) const { return reinterpret_cast<const uint4*>(W)[grp * 32 + lane]; }
 };
 struct WordsReg {
     uint32_t w[kMlpWords];
     __device__ __forceinline__ WordsReg(const uint32_t* W, int lane) {
 #pragma unroll
-        for (int k = 0; k < kMlpWords; k++) w[k] = W[k * 32 + lane];
+        for (int k = 0; k < kMlpWords; k++) w[k] = W[frag_index(k, lane)];
     }
     __device__ __forceinline__ uint32_t operator()(int k) const { return w[k]; }
+    __device__ __forceinline__ uint4 q(int grp) const {
+        return make_uint4(w[4 * grp], w[4 * grp + 1], w[4 * grp + 2], w[4 * grp + 3]);
+    }
 };
 
 // K row tiles of 16 starting at tile mt0, their products interleaved (K
@@ -129,7 +137,6 @@ template <int K, class Words>
 __device__ __forceinline__ void mlp_tiles(const Words& W, const uint32_t* __restrict__ in, float* __restrict__ om,
                                           int lane, int mt0) {
     const int g = lane >> 2, t = lane & 3;
-    auto Wf = [&](int k) { return __uint_as_float(W(k)); };
     uint32_t a0[K], a1[K];
 #pragma unroll
     for (int q = 0; q < K; q++) {
@@ -138,11 +145,13 @@ __device__ __forceinline__ void mlp_tiles(const Words& W, const uint32_t* __rest
         a1[q] = in[(r0 + 8) * 4 + t];
     }
     float c1[K][4][4];
+    {
+        const uint4 w1 = W.q(0);
+        const uint32_t b[4] = {w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-    for (int nt = 0; nt < 4; nt++) {
-        const uint32_t b = W(nt);
+        for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-        for (int q = 0; q < K; q++) mma_k8_c(c1[q][nt], a0[q], a1[q], b, 0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < K; q++) mma_k8_c(c1[q][nt], a0[q], a1[q], b[nt], 0.f, 0.f, 0.f, 0.f);
     }
     uint32_t A2[K][2][4];
 #pragma unroll
@@ -155,14 +164,18 @@ __device__ __forceinline__ void mlp_tiles(const Words& W, const uint32_t* __rest
             A2[q][kt][3] = gelu_k(c1[q][2 * kt + 1][2], c1[q][2 * kt + 1][3]);
         }
     float c2[K][4][4];
+    {
+        const uint4 bb0 = W.q(6), bb1 = W.q(7);      // hidden bias pairs of n tiles 0, 1 and 2, 3
+        const uint32_t bias[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
 #pragma unroll
-    for (int nt = 0; nt < 4; nt++) {
-        const float blo = Wf(24 + 2 * nt), bhi = Wf(25 + 2 * nt);
-        const uint32_t b0 = W(4 + nt * 4), b1 = W(5 + nt * 4), b2 = W(6 + nt * 4), b3 = W(7 + nt * 4);
+        for (int nt = 0; nt < 4; nt++) {
+            const float blo = __uint_as_float(bias[2 * nt]), bhi = __uint_as_float(bias[2 * nt + 1]);
+            const uint4 w2 = W.q(1 + nt);
 #pragma unroll
-        for (int q = 0; q < K; q++) {
-            mma_k16_c(c2[q][nt], A2[q][0], b0, b1, blo, bhi, blo, bhi);
-            mma_k16(c2[q][nt], A2[q][1], b2, b3);
+            for (int q = 0; q < K; q++) {
+                mma_k16_c(c2[q][nt], A2[q][0], w2.x, w2.y, blo, bhi, blo, bhi);
+                mma_k16(c2[q][nt], A2[q][1], w2.z, w2.w);
+            }
         }
     }
     uint32_t A3[K][2][4];
@@ -175,14 +188,14 @@ __device__ __forceinline__ void mlp_tiles(const Words& W, const uint32_t* __rest
             A3[q][kt][2] = gelu_k(c2[q][2 * kt + 1][0], c2[q][2 * kt + 1][1]);
             A3[q][kt][3] = gelu_k(c2[q][2 * kt + 1][2], c2[q][2 * kt + 1][3]);
         }
-    const float b3lo = Wf(32), b3hi = Wf(33);
     float c3[K][4];
     {
-        const uint32_t b0 = W(20), b1 = W(21), b2 = W(22), b3 = W(23);
+        const uint4 w3 = W.q(5), b3 = W.q(8);
+        const float b3lo = __uint_as_float(b3.x), b3hi = __uint_as_float(b3.y);
 #pragma unroll
         for (int q = 0; q < K; q++) {
-            mma_k16_c(c3[q], A3[q][0], b0, b1, b3lo, b3hi, b3lo, b3hi);
-            mma_k16(c3[q], A3[q][1], b2, b3);
+            mma_k16_c(c3[q], A3[q][0], w3.x, w3.y, b3lo, b3hi, b3lo, b3hi);
+            mma_k16(c3[q], A3[q][1], w3.z, w3.w);
         }
     }
 #pragma unroll
@@ -336,14 +349,16 @@ struct LearnedWeights {
     // and the split fluxes are their running sums up to a constant, which
     // the network's input normalisation (v - mean v) / max|v - mean v|
     // does not see.
+    // The split differences are taken twice over (dg +- alpha dw, the
+    // Jiang-Shu sweep's exact scaling): the inputs' normalisation and the
+    // detectors do not see the factor, the gate and phi_N take 4 eps, and
+    // corr_vd halves its result.
     __device__ __forceinline__ float corr_d(int s, const float (&dw)[5], const float (&dg)[5], float alpha) {
-        const float ha = 0.5f * alpha;
         float dP[5], dM[5];
 #pragma unroll
         for (int m = 0; m < 5; m++) {
-            const float hg = 0.5f * dg[m];
-            dP[m] = fmaf(ha, dw[m], hg);
-            dM[m] = fmaf(-ha, dw[m], hg);
+            dP[m] = fmaf(alpha, dw[m], dg[m]);
+            dM[m] = fmaf(-alpha, dw[m], dg[m]);
         }
         float2 D[4], V[6];
         V[0] = splat2(0.0f);
@@ -353,28 +368,15 @@ struct LearnedWeights {
             if (k < 4) D[k] = d;
             V[k + 1] = __fadd2_rn(V[k], d);
         }
-        return corr_vd(s, V, D);
+        return corr_vd<true>(s, V, D);
     }
 
     // Lane x the '+' side, lane y the '-' side with its stencil reversed:
-    // V the six split fluxes (up to a constant), D their four differences.
+    // V the six split fluxes (up to a constant), D their four differences;
+    // TWICE: both taken twice over.
+    template <bool TWICE = false>
     __device__ __forceinline__ float corr_vd(int s, const float2 (&V)[6], const float2 (&D)[4]) {
-        float2 mean = V[0];
-#pragma unroll
-        for (int k = 1; k < 6; k++) mean = __fadd2_rn(mean, V[k]);
-        mean = __fmul2_rn(mean, splat2(1.0f / 6.0f));
-        float2 dv[6];
-        float mxp = 0.f, mxm = 0.f;
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            dv[k] = __ffma2_rn(mean, splat2(-1.0f), V[k]);
-            mxp = fmaxf(mxp, fabsf(dv[k].x));
-            mxm = fmaxf(mxm, fabsf(dv[k].y));
-        }
-        const float2 inv = make_float2(__fdividef(1.0f, mxp + 1e-12f), __fdividef(1.0f, mxm + 1e-12f));
-        float2 x[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) x[k] = __fmul2_rn(dv[k], inv);
+        constexpr float kEps3 = TWICE ? 4.0f * kEps3f : kEps3f;
         bool fire[2];
 #pragma unroll
         for (int side = 0; side < 2; side++) {
@@ -389,17 +391,19 @@ struct LearnedWeights {
         }
         {
             // smoothness gate on both sides at once (the indicators are even
-            // in D, so lane y's negated differences give the '-' side's)
+            // in D, so lane y's negated differences give the '-' side's),
+            // compared as (eps + IS_k)/3 like phi_N forms them
+            const float2 k13 = splat2(13.0f / 3.0f), eps3 = splat2(kEps3);
             const float2 t0 = __ffma2_rn(D[1], splat2(-1.0f), D[0]), t1 = __ffma2_rn(D[1], splat2(-3.0f), D[0]);
             const float2 t2 = __ffma2_rn(D[2], splat2(-1.0f), D[1]), t3 = __fadd2_rn(D[1], D[2]);
-            const float2 t4 = __ffma2_rn(D[3], splat2(-1.0f), D[2]), t5 = __ffma2_rn(D[2], splat2(3.0f), __fmul2_rn(D[3], splat2(-1.0f)));
-            const float2 is0 = __ffma2_rn(__fmul2_rn(t0, splat2(13.0f)), t0, __fmul2_rn(__fmul2_rn(t1, splat2(3.0f)), t1));
-            const float2 is1 = __ffma2_rn(__fmul2_rn(t2, splat2(13.0f)), t2, __fmul2_rn(__fmul2_rn(t3, splat2(3.0f)), t3));
-            const float2 is2 = __ffma2_rn(__fmul2_rn(t4, splat2(13.0f)), t4, __fmul2_rn(__fmul2_rn(t5, splat2(3.0f)), t5));
-            const float mxp = fmaxf(is0.x, fmaxf(is1.x, is2.x)), mnp = fminf(is0.x, fminf(is1.x, is2.x));
-            const float mxm = fmaxf(is0.y, fmaxf(is1.y, is2.y)), mnm = fminf(is0.y, fminf(is1.y, is2.y));
-            fire[0] = fire[0] || !(mxp + 1e-6f > smooth * (mnp + 1e-6f));
-            fire[1] = fire[1] || !(mxm + 1e-6f > smooth * (mnm + 1e-6f));
+            const float2 t4 = __ffma2_rn(D[3], splat2(-1.0f), D[2]), t5 = __ffma2_rn(D[2], splat2(-3.0f), D[3]);
+            const float2 e0 = __ffma2_rn(__fmul2_rn(t0, k13), t0, __ffma2_rn(t1, t1, eps3));
+            const float2 e1 = __ffma2_rn(__fmul2_rn(t2, k13), t2, __ffma2_rn(t3, t3, eps3));
+            const float2 e2 = __ffma2_rn(__fmul2_rn(t4, k13), t4, __ffma2_rn(t5, t5, eps3));
+            const float mxp = fmaxf(e0.x, fmaxf(e1.x, e2.x)), mnp = fminf(e0.x, fminf(e1.x, e2.x));
+            const float mxm = fmaxf(e0.y, fmaxf(e1.y, e2.y)), mnm = fminf(e0.y, fminf(e1.y, e2.y));
+            fire[0] = fire[0] || !(mxp > smooth * mnp);
+            fire[1] = fire[1] || !(mxm > smooth * mnm);
             nfire += (fire[0] ? 1 : 0) + (fire[1] ? 1 : 0);
         }
         // the network on the rows that use its weights only: the warp's
@@ -411,6 +415,23 @@ struct LearnedWeights {
         const int npl = __popc(mp), nrow = npl + __popc(mm);
         float2 w0 = splat2(0.0f), w2 = splat2(0.0f);
         if (nrow > 0) {
+            // the network's inputs, normalised, for warps with rows that use it
+            float2 mean = V[0];
+#pragma unroll
+            for (int k = 1; k < 6; k++) mean = __fadd2_rn(mean, V[k]);
+            mean = __fmul2_rn(mean, splat2(1.0f / 6.0f));
+            float2 dv[6];
+            float mxp = 0.f, mxm = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                dv[k] = __ffma2_rn(mean, splat2(-1.0f), V[k]);
+                mxp = fmaxf(mxp, fabsf(dv[k].x));
+                mxm = fmaxf(mxm, fabsf(dv[k].y));
+            }
+            const float2 inv = make_float2(__fdividef(1.0f, mxp + 1e-12f), __fdividef(1.0f, mxm + 1e-12f));
+            float2 x[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) x[k] = __fmul2_rn(dv[k], inv);
             const int rp = __popc(mp & lt), rm = npl + __popc(mm & lt);
             if (!fire[0])
                 *reinterpret_cast<uint4*>(in + rp * 4) =
@@ -432,12 +453,12 @@ struct LearnedWeights {
         float2 ph = __ffma2_rn(__fmul2_rn(w0, splat2(1.0f / 3.0f)), pp,
                                __fmul2_rn(__fmul2_rn(__fadd2_rn(w2, splat2(-0.5f)), splat2(1.0f / 6.0f)), qq));
         if (fire[0] || fire[1]) {
-            const float2 js = phi_n2(D[0], D[1], D[2], D[3]);
+            const float2 js = phi_n2(D[0], D[1], D[2], D[3], kEps3);
             if (fire[0]) ph.x = js.x;
             if (fire[1]) ph.y = js.y;
         }
         // phm - php with phm = -(value on -D-)
-        return -ph.y - ph.x;
+        return TWICE ? -0.5f * (ph.y + ph.x) : -ph.y - ph.x;
     }
 };
 
@@ -632,27 +653,30 @@ void mlp_fragments(const float* params, uint32_t* out) {
         auto w3 = [&](int n, int k) { return n < 3 ? W3[n * NH + k] / (2.0f * kGeluK) : 0.f; };
         for (int lane = 0; lane < 32; lane++) {
             const int g = lane >> 2, t = lane & 3;
-            uint32_t* o = out + (size_t)f * kMlpWords * 32 + lane;
-            for (int nt = 0; nt < 4; nt++) o[nt * 32] = pk(w1(8 * nt + g, 2 * t), w1(8 * nt + g, 2 * t + 1));
+            uint32_t* of = out + (size_t)f * kMlpWords * 32;
+            auto o = [&](int k) -> uint32_t& { return of[frag_index(k, lane)]; };
+            o(34) = 0u;
+            o(35) = 0u;
+            for (int nt = 0; nt < 4; nt++) o(nt) = pk(w1(8 * nt + g, 2 * t), w1(8 * nt + g, 2 * t + 1));
             for (int nt = 0; nt < 4; nt++)
                 for (int kt = 0; kt < 2; kt++) {
                     const int n = 8 * nt + g, k0 = 16 * kt + 2 * t;
                     // hidden weights halved: the layer's input is 2 kGeluK gelu, its
                     // output is wanted times kGeluK
-                    o[(4 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0], 0.5f * W2[n * NH + k0 + 1]);
-                    o[(5 + nt * 4 + kt * 2) * 32] = pk(0.5f * W2[n * NH + k0 + 8], 0.5f * W2[n * NH + k0 + 9]);
+                    o(4 + nt * 4 + kt * 2) = pk(0.5f * W2[n * NH + k0], 0.5f * W2[n * NH + k0 + 1]);
+                    o(5 + nt * 4 + kt * 2) = pk(0.5f * W2[n * NH + k0 + 8], 0.5f * W2[n * NH + k0 + 9]);
                 }
             for (int kt = 0; kt < 2; kt++) {
                 const int k0 = 16 * kt + 2 * t;
-                o[(20 + kt * 2) * 32] = pk(w3(g, k0), w3(g, k0 + 1));
-                o[(21 + kt * 2) * 32] = pk(w3(g, k0 + 8), w3(g, k0 + 9));
+                o(20 + kt * 2) = pk(w3(g, k0), w3(g, k0 + 1));
+                o(21 + kt * 2) = pk(w3(g, k0 + 8), w3(g, k0 + 9));
             }
             for (int nt = 0; nt < 4; nt++) {
-                o[(24 + 2 * nt) * 32] = fbits(kGeluK * b2[8 * nt + 2 * t]);
-                o[(25 + 2 * nt) * 32] = fbits(kGeluK * b2[8 * nt + 2 * t + 1]);
+                o(24 + 2 * nt) = fbits(kGeluK * b2[8 * nt + 2 * t]);
+                o(25 + 2 * nt) = fbits(kGeluK * b2[8 * nt + 2 * t + 1]);
             }
-            o[32 * 32] = fbits(2 * t < 3 ? b3[2 * t] : 0.f);
-            o[33 * 32] = fbits(2 * t + 1 < 3 ? b3[2 * t + 1] : 0.f);
+            o(32) = fbits(2 * t < 3 ? b3[2 * t] : 0.f);
+            o(33) = fbits(2 * t + 1 < 3 ? b3[2 * t + 1] : 0.f);
         }
     }
 }
