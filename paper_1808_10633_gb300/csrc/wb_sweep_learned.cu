@@ -13,8 +13,9 @@
 // a seventh input equal to 1) and mma.sync.m16n8k16 (hidden and output
 // layers), BF16 operands and FP32 accumulators.  A layer's accumulator
 // fragments are re-packed in registers as the next layer's A fragments; the
-// weights sit in shared memory already in B-fragment order (34 words per lane
-// per field, written by wb_set_mlp on the host side).  The GELU (sigmoid
+// weights are stored already in B-fragment order (34 words per lane per
+// field in groups of four, so that a warp reads each group as one 16-byte
+// load per lane; written by wb_set_mlp on the host side).  The GELU (sigmoid
 // form) takes one hardware tanh and one FMA on BF16 pairs, the constant of
 // its argument folded into the stored weights (gelu_k).  Batch rows are
 // independent, so a lane whose interface lies outside the patch still joins
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kLearnedNT, WB_LEARNED_MINB) sweep_learned_ker
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
 #if WB_LEARNED_DELTA
-    // weight fragments read from global memory (L1-resident, 30.5 KB); each
+    // weight fragments read from global memory (L1-resident, 32 KB); each
     // thread's back-projection and parked slots after the staged cells
     const uint32_t* Wsm = mlp;
     uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + (kNSlot * NC + kNThreadSlots * TA * TP));
