@@ -341,8 +341,11 @@ def run_native(args, rank, world, local):
         el = time.perf_counter() - t0
         barrier(world)
         el = max_over_ranks(el, world)
+        # bytes over the host link: the import reads rho, m, E of U and the
+        # three face arrays of b (U's cell-centred B follows from the faces);
+        # the export writes all of U and b
         e2e = {"value": world * zones * args.steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": int(Uh.numel() * 4 + bh.numel() * 4),
+               "h2d_bytes_per_step": int(8 * zones * 4),
                "d2h_bytes_per_step": int(Uo.numel() * 4 + bo.numel() * 4),
                "path": "wb_set_state_f32(pinned) + wb_step_cfl(1) + wb_get_state_f32(pinned), "
                        "the whole state in and out every step"}
