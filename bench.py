@@ -298,7 +298,7 @@ def run_native(args, rank, world, local):
     if g64 is not None:
         g64.close()
 
-    # ---- batched uneven patches (config 4) --------------------------------
+    # ---- 4096 batched uneven periodic patches (edges 16-64) ------------------
     patches = None
     if args.patches > 0:
         patches = run_patches(args, world)
@@ -308,12 +308,12 @@ def run_native(args, rank, world, local):
     if not args.no_linked:
         linked = run_linked(args, st, world)
 
-    # ---- 512^3 turbulence + blasts, sweep kernels only (config 3) -----------
+    # ---- 512^3 turbulence + blasts, sweep kernels only ----------------------
     large = None
     if args.large_size > 0:
         large = run_large(args, world)
 
-    # ---- learned weights on turbulence + blasts (config 5) -----------------
+    # ---- learned weights on 256^3 turbulence + blasts ----------------------
     learned = None
     if not args.no_learned:
         args.sm_mhz = clk.get("sm_mhz")
