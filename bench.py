@@ -384,6 +384,16 @@ def run_native(args, rank, world, local):
         "large": large,
         "linked": linked,
     })
+    # the other legs' headline rates in one short object at the end of the line
+    out["legs"] = {
+        "fp64": out["fp64"]["value"] if out["fp64"] else None,
+        "e2e": e2e["value"] if e2e else None,
+        "learned": learned["value"] if learned else None,
+        "learned_gain_vs_js": learned.get("gain_vs_js") if learned else None,
+        "patches": patches["value"] if patches else None,
+        "large_whole_step": large.get("value_whole_step") if large else None,
+        "linked": linked["value"] if linked else None,
+    }
     return out
 
 
@@ -743,6 +753,8 @@ def main():
         res["cpu_baseline"]["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
                                               "sample": f"{s1} steps of a 32^3 sample, {el1:.1f} s wall"}
     if rank == 0:
+        if "legs" in res:
+            res["legs"] = res.pop("legs")          # keep the short summary last
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist
