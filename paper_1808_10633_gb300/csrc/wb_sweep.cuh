@@ -56,8 +56,20 @@ template <class T> __device__ __forceinline__ T sq_root(T x);
 template <> __device__ __forceinline__ float sq_root<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double sq_root<double>(double x) { return sqrt(x); }
 
+template <class T> __device__ __forceinline__ T rsq_root(T x);
+template <> __device__ __forceinline__ float rsq_root<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq_root<double>(double x) { return rsqrt(x); }
+
 template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <class T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+// |a| by clearing the sign bit (no floating-point compare on the FP64 pipe)
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+// max of two values >= 0: for non-negative IEEE values the bit patterns
+// order like the values, so FP64 takes an integer max, off the FP64 pipe
+__device__ __forceinline__ float tmax_nonneg(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax_nonneg(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
 
 __device__ __forceinline__ int wrap(int v, int n) {
     int r = v % n;
@@ -88,6 +100,44 @@ __device__ __forceinline__ double phi_n(double a, double b, double c, double d, 
 }
 
 constexpr float kEps3f = 1e-6f / 3.0f;
+// phi_N(am, bm, cm, dm) - phi_N(ap, bp, cp, dp) in FP64 with one division
+// for both: each side's weights are n_k / den, and the two denominators
+// share the reciprocal of their product (falling back to one division each
+// where that product would leave the FP64 range).
+__device__ __forceinline__ void phi_n_parts(double a, double b, double c, double d, double eps3, double& n0,
+                                            double& n2, double& den) {
+    const double k13 = 13.0 / 3.0;
+    const double t0 = a - b, t1 = a - 3.0 * b;
+    const double t2 = b - c, t3 = b + c;
+    const double t4 = c - d, t5 = 3.0 * c - d;
+    double e0 = fma(k13 * t0, t0, fma(t1, t1, eps3));
+    double e1 = fma(k13 * t2, t2, fma(t3, t3, eps3));
+    double e2 = fma(k13 * t4, t4, fma(t5, t5, eps3));
+    e0 *= e0; e1 *= e1; e2 *= e2;
+    n0 = e1 * e2;
+    n2 = 3.0 * e0 * e1;
+    den = n0 + 6.0 * e0 * e2 + n2;
+}
+__device__ __forceinline__ double phi_n_diff(double am, double bm, double cm, double dm, double ap, double bp,
+                                             double cp, double dp, double eps3) {
+    double n0m, n2m, denm, n0p, n2p, denp;
+    phi_n_parts(am, bm, cm, dm, eps3, n0m, n2m, denm);
+    phi_n_parts(ap, bp, cp, dp, eps3, n0p, n2p, denp);
+    const double prod = denm * denp;
+    double rm, rp;
+    if (prod < 1e300) {
+        const double R = 1.0 / prod;
+        rm = denp * R;
+        rp = denm * R;
+    } else {
+        rm = 1.0 / denm;
+        rp = 1.0 / denp;
+    }
+    const double phm = n0m * rm * (am - 2.0 * bm + cm) * (1.0 / 3.0) + (n2m * rm - 0.5) * (bm - 2.0 * cm + dm) * (1.0 / 6.0);
+    const double php = n0p * rp * (ap - 2.0 * bp + cp) * (1.0 / 3.0) + (n2p * rp - 0.5) * (bp - 2.0 * cp + dp) * (1.0 / 6.0);
+    return phm - php;
+}
+
 __device__ __forceinline__ float phi_n(float a, float b, float c, float d, float eps3 = kEps3f) {
     const float k13 = 13.0f / 3.0f;
     const float t0 = a - b, t1 = a - 3.0f * b;
@@ -229,6 +279,8 @@ __device__ __forceinline__ T weno_corr_d(const T (&dw)[5], const T (&dg)[5], T a
             const float2 ph = phi_n2(make_float2(dm4, dp0), make_float2(dm3, dp1), make_float2(dm2, dp2),
                                      make_float2(dm1, dp3), eps3);
             return T(0.5) * (ph.x - ph.y);
+        } else if constexpr (sizeof(T) == 8) {
+            return T(0.5) * phi_n_diff(dm4, dm3, dm2, dm1, dp0, dp1, dp2, dp3, eps3);
         } else {
             return T(0.5) * (phi_n(dm4, dm3, dm2, dm1, eps3) - phi_n(dp0, dp1, dp2, dp3, eps3));
         }
@@ -304,9 +356,9 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
     double bp2 = b1 * b1 + b2 * b2;
     double bt2 = bn * bn + bp2;
     if (bp2 > 1e-24 * (bt2 > 1.0 ? bt2 : 1.0)) {
-        double bp = sqrt(bp2);
-        be1 = b1 / bp;
-        be2 = b2 / bp;
+        const double ibp = rsqrt(bp2);
+        be1 = b1 * ibp;
+        be2 = b2 * ibp;
     } else {
         be1 = be2 = 0.70710678118654752440;
     }
@@ -330,8 +382,9 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
         double y = 0.5 * (D - (a2 - ca2) + t);
         if (x >= y) y = a2 * t / x;
         else x = a2 * t / y;
-        alf = sqrt(x > 0.0 ? x / D : 0.0);
-        als = sqrt(y > 0.0 ? y / D : 0.0);
+        const double iD = 1.0 / D;
+        alf = sqrt(x > 0.0 ? x * iD : 0.0);
+        als = sqrt(y > 0.0 ? y * iD : 0.0);
     }
     cf2o = cf2;
     cs2o = cs2;
@@ -340,7 +393,7 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
 template <class T>
 __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, T p, T gamma,
                                       Eig<T>& e, T* __restrict__ bp, int bstride) {
-    const T rinv = T(1) / rho;
+    const T isr = rsq_root(rho), rinv = isr * isr;     // 1/sqrt(rho), 1/rho
     const T a2 = gamma * p * rinv;
     const T ca2 = bn * bn * rinv;
     T cf2, cs2, be1, be2, alf, als;
@@ -367,9 +420,9 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
             be1 = T(dbe1); be2 = T(dbe2); alf = T(dalf); als = T(dals);
             cf2 = T(dcf2); cs2 = T(dcs2);
         } else {
-            const T bp = sq_root(bp2);
-            be1 = b1 / bp;
-            be2 = b2 / bp;
+            const T ibp = rsq_root(bp2);
+            be1 = b1 * ibp;
+            be2 = b2 * ibp;
             T x = T(0.5) * (D + (a2 - ca2) - t), y = T(0.5) * (D - (a2 - ca2) + t);
             if (x >= y) y = a2 * t / x;
             else x = a2 * t / y;
@@ -379,14 +432,17 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
         }
     }
     const T cf = sq_root(cf2), cs = sq_root(cs2), ca = sq_root(ca2);
-    const T a = sq_root(a2), sr = sq_root(rho);
+    // sqrt(rho), sqrt(a^2) and their reciprocals from one reciprocal square
+    // root each (isr above)
+    const T ia = rsq_root(a2);
+    const T sr = rho * isr, a = a2 * ia;
     const T S = bn >= T(0) ? T(1) : T(-1);
     const T gm1 = gamma - T(1);
     const T X = alf * alf * cf2 + als * als * cs2;
     const T hXr = T(0.5) / X * rinv;
-    const T isr = T(1) / sr;
-    const T hia = T(0.5) / a * isr;          // 1 / (2 a sqrt(rho))
-    const T hgp = T(0.5) * gm1 / (gamma * p); // (gamma-1) / (2 rho a^2)
+    const T hia = T(0.5) * ia * isr;         // 1 / (2 a sqrt(rho))
+    const T Ee = gm1 * ia * ia;              // (gamma-1) / a^2
+    const T hgp = T(0.5) * Ee * rinv;        // (gamma-1) / (2 rho a^2)
     e.rho = rho; e.u = u; e.v1 = v1; e.v2 = v2; e.b1 = b1; e.b2 = b2;
     e.hv2 = T(0.5) * (u * u + v1 * v1 + v2 * v2);
     e.be1 = be1; e.be2 = be2;
@@ -409,7 +465,7 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
     e.Ds = als * hgp;
     e.Aa = T(0.5) * rinv;
     e.Ba = T(0.5) * S * isr;
-    e.Ee = gm1 / a2;
+    e.Ee = Ee;
 }
 
 // ---- staging ---------------------------------------------------------------
@@ -666,7 +722,7 @@ __device__ __forceinline__ T lf_speed(const T* __restrict__ sm, int nc, const in
                                       int s, T lam_avg) {
     T al = lam_avg;
 #pragma unroll
-    for (int m = 0; m < 6; m++) al = tmax(al, sm[(SL + s) * nc + id[m]]);
+    for (int m = 0; m < 6; m++) al = tmax_nonneg(al, sm[(SL + s) * nc + id[m]]);
     return al;
 }
 
