@@ -396,12 +396,12 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
     const T isr = rsq_root(rho), rinv = isr * isr;     // 1/sqrt(rho), 1/rho
     const T a2 = gamma * p * rinv;
     const T ca2 = bn * bn * rinv;
-    T cf2, cs2, be1, be2, alf, als;
+    T cf2, be1, be2, alf, als;
     if constexpr (sizeof(T) == 8) {
         double dbe1, dbe2, dalf, dals, dcf2, dcs2;
         degenerate_rules(rho, bn, b1, b2, p, gamma, dbe1, dbe2, dalf, dals, dcf2, dcs2);
         be1 = T(dbe1); be2 = T(dbe2); alf = T(dalf); als = T(dals);
-        cf2 = T(dcf2); cs2 = T(dcs2);
+        cf2 = T(dcf2);
     } else {
         // FP32 bulk; the normalisation near B_perp -> 0 and near cf = cs
         // (fast/slow/Alfven coincidence) is taken in FP64.
@@ -411,14 +411,13 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
         const T t = bp2 * rinv;
         const T D = sq_root((a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t));
         cf2 = T(0.5) * ((a2 + ca2 + t) + D);
-        cs2 = cf2 > T(0) ? a2 * ca2 / cf2 : T(0);
         const bool near_bperp = !(bp2 > T(1e-6) * bt2);
         const bool near_triple = !(D > T(1e-3) * (a2 + b2r));
         if (near_bperp || near_triple) {
             double dbe1, dbe2, dalf, dals, dcf2, dcs2;
             degenerate_rules(rho, bn, b1, b2, p, gamma, dbe1, dbe2, dalf, dals, dcf2, dcs2);
             be1 = T(dbe1); be2 = T(dbe2); alf = T(dalf); als = T(dals);
-            cf2 = T(dcf2); cs2 = T(dcs2);
+            cf2 = T(dcf2);
         } else {
             const T ibp = rsq_root(bp2);
             be1 = b1 * ibp;
@@ -431,11 +430,14 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
             als = sq_root(tmax(y * r, T(0)));
         }
     }
-    const T cf = sq_root(cf2), cs = sq_root(cs2), ca = sq_root(ca2);
-    // sqrt(rho), sqrt(a^2) and their reciprocals from one reciprocal square
-    // root each (isr above)
+    // sqrt(rho), sqrt(a^2), cf and their reciprocals from one reciprocal
+    // square root each (isr above); ca = |B_n| / sqrt(rho) and, from the
+    // product of the roots cf^2 cs^2 = a^2 ca^2, cs = a ca / cf
     const T ia = rsq_root(a2);
     const T sr = rho * isr, a = a2 * ia;
+    const T icf = cf2 > T(0) ? rsq_root(cf2) : T(0);
+    const T cf = cf2 * icf, ca = tabs(bn) * isr;
+    const T cs = a * ca * icf, cs2 = cs * cs;
     const T S = bn >= T(0) ? T(1) : T(-1);
     const T gm1 = gamma - T(1);
     const T X = alf * alf * cf2 + als * als * cs2;
@@ -535,7 +537,7 @@ __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell
     else if (AXIS == 1) { mn = my; m1 = mz; m2 = mx; bn = By; b1 = Bz; b2 = Bx; }
     else { mn = mz; m1 = mx; m2 = my; bn = Bz; b1 = Bx; b2 = By; }
     const T g = T(A.gamma);
-    const T rinv = T(1) / rho;
+    const T isr = rsq_root(rho), rinv = isr * isr;
     const T u = mn * rinv, v1 = m1 * rinv, v2 = m2 * rinv;
     const T bb = bn * bn + b1 * b1 + b2 * b2;
     const T kin = T(0.5) * (mn * u + m1 * v1 + m2 * v2);
@@ -564,9 +566,10 @@ __device__ __forceinline__ void derive_cell(const SweepArgs<T>& A, const RawCell
     const T t = (b1 * b1 + b2 * b2) * rinv;
     const T D = sq_root((a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t));
     const T cf2 = T(0.5) * ((a2 + ca2 + t) + D);
-    const T cf = sq_root(cf2);
-    const T cs = sq_root(cf2 > T(0) ? a2 * ca2 / cf2 : T(0));
-    const T ca = sq_root(ca2);
+    const T icf = cf2 > T(0) ? rsq_root(cf2) : T(0);
+    const T cf = cf2 * icf;
+    const T ca = tabs(bn) * isr;
+    const T cs = sq_root(a2) * ca * icf;       // sqrt(a^2 ca^2 / cf^2)
     sm[(SL + 0) * nc + idx] = tabs(u - cf);
     sm[(SL + 1) * nc + idx] = tabs(u - ca);
     sm[(SL + 2) * nc + idx] = tabs(u - cs);
