@@ -372,7 +372,10 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
     // x, y from x + y = D and the smaller from x y = a^2 t, so the vanishing
     // weight goes to zero with B_perp
     const double t = bp2 / rho;
-    const double D = sqrt((a2 - ca2) * (a2 - ca2) + t * (2.0 * (a2 + ca2) + t));
+    // D and 1/D from one reciprocal square root (D = 0 kept exact)
+    const double D2 = (a2 - ca2) * (a2 - ca2) + t * (2.0 * (a2 + ca2) + t);
+    const double iD = D2 > 0.0 ? rsqrt(D2) : 0.0;
+    const double D = D2 * iD;
     const double cf2 = 0.5 * ((a2 + ca2 + t) + D);
     const double cs2 = cf2 > 0.0 ? a2 * ca2 / cf2 : 0.0;
     if (D <= 1e-12 * (a2 + b2r)) {
@@ -382,7 +385,6 @@ __device__ __forceinline__ void degenerate_rules(double rho, double bn, double b
         double y = 0.5 * (D - (a2 - ca2) + t);
         if (x >= y) y = a2 * t / x;
         else x = a2 * t / y;
-        const double iD = 1.0 / D;
         alf = sqrt(x > 0.0 ? x * iD : 0.0);
         als = sqrt(y > 0.0 ? y * iD : 0.0);
     }
@@ -409,7 +411,9 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
         const T bt2 = bn * bn + bp2;
         const T b2r = bt2 * rinv;
         const T t = bp2 * rinv;
-        const T D = sq_root((a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t));
+        const T D2 = (a2 - ca2) * (a2 - ca2) + t * (T(2) * (a2 + ca2) + t);
+        const T iD = D2 > T(0) ? rsq_root(D2) : T(0);
+        const T D = D2 * iD;
         cf2 = T(0.5) * ((a2 + ca2 + t) + D);
         const bool near_bperp = !(bp2 > T(1e-6) * bt2);
         const bool near_triple = !(D > T(1e-3) * (a2 + b2r));
@@ -425,9 +429,8 @@ __device__ __forceinline__ void eigen(T rho, T u, T v1, T v2, T bn, T b1, T b2, 
             T x = T(0.5) * (D + (a2 - ca2) - t), y = T(0.5) * (D - (a2 - ca2) + t);
             if (x >= y) y = a2 * t / x;
             else x = a2 * t / y;
-            const T r = T(1) / D;
-            alf = sq_root(tmax(x * r, T(0)));
-            als = sq_root(tmax(y * r, T(0)));
+            alf = sq_root(tmax(x * iD, T(0)));
+            als = sq_root(tmax(y * iD, T(0)));
         }
     }
     // sqrt(rho), sqrt(a^2), cf and their reciprocals from one reciprocal
