@@ -50,8 +50,8 @@ SWEEP_FLOPS_PER_STAGED_CELL = 80
 # benchmark times (profiles/sweep_traffic_fp32_turbulence256.md); reported
 # only at that size and while the sweep sources hash to SWEEP_TRAFFIC_SOURCES.
 SWEEP_TRAFFIC_N = 256
-SWEEP_TRAFFIC = {"sweep_x": 1180.62e6, "sweep_y": 980.97e6, "sweep_z": 978.51e6}
-SWEEP_TRAFFIC_SOURCES = "cfe74a642270946d"
+SWEEP_TRAFFIC = {"sweep_x": 1180.90e6, "sweep_y": 980.41e6, "sweep_z": 978.70e6}
+SWEEP_TRAFFIC_SOURCES = "69dc94dc5fccf3ed"
 
 
 def sweep_sources_hash() -> str:
