@@ -60,6 +60,21 @@ def test_fp64_one_step_ragged_tiles(orc, wb, dims):
     compare(orc, wb, st, 2e-3)
 
 
+def test_fp64_large_magnitude_state(orc, wb):
+    """Ideal MHD is unchanged by v, B -> V v, V B, p, E -> V^2 p, V^2 E and
+    t -> t / V.  At V = 1e9 the energy fluxes reach ~1e27, the smoothness
+    indicators ~1e54 and the product of the two weight denominators of a
+    field's phi_N pair overflows FP64, so the FP64 sweep takes its path with
+    one division per side; the step must still match the oracle."""
+    V = 1e9
+    st = I.perturbed(24, 12, 10, seed=31, jump=True)
+    U = st.U.copy()
+    U[1:7] *= V
+    U[7] *= V * V
+    big = I.State(U, st.bx * V, st.by * V, st.bz * V, st.dx, st.dy, st.dz, st.gamma, st.meta)
+    compare(orc, wb, big, 2e-3 / V)
+
+
 def test_fp64_three_steps_emf_modes(orc, wb):
     st = I.perturbed(24, 20, 16, seed=5, jump=True)
     compare(orc, wb, st, 2e-3, nsteps=3, emf_mode=0)
